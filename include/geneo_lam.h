@@ -1,0 +1,183 @@
+/*
+ * geneo_lam.h -- C ABI of the GB300 GenEO-PCG solver for layered laminates.
+ *
+ * The library solves K u = f (Section 2.3, Eq. eq-1) for 3D anisotropic
+ * linear elasticity on a layered, structured hexahedral laminate (Section 2.1,
+ * "dune-composites"), discretised with 27-node triquadratic (Q2) hexahedra and
+ * full 3x3x3 Gauss integration, by conjugate gradients (Section 2.3) on the
+ * preconditioned system P K u = P f (Eq. eq-pre), where P is the two-level
+ * overlapping additive Schwarz preconditioner with the GenEO coarse space
+ * (Section 2.3, Fig. domaindecomp, Fig. eig).  Stresses sigma_33 = sigma_r and
+ * tau_13 = tau_rs (Section 2.2 notation, Eq. eq-Camanho) are recovered at
+ * element centres.
+ *
+ * Conventions (all entry points):
+ *   units      N, mm, MPa.
+ *   mesh       nx x ny x nz elements, e = ex + nx*(ey + ny*ez); z is the
+ *              thickness (r) direction, x the s direction, y the width l.
+ *   nodes      (2nx+1)(2ny+1)(2nz+1), n = ix + NX*(iy + NY*iz), x fastest.
+ *   DOFs       N = 3 * nodes, dof = 3*n + component (node-major).
+ *   faces      0 -s, 1 +s, 2 -l, 3 +l, 4 -r (inner/bottom), 5 +r (outer/top).
+ *   pointers   every array argument may be host memory or CUDA device memory
+ *              of the context's device; the library tells them apart with
+ *              cudaPointerGetAttributes.  Input arrays are caller-owned and
+ *              copied before the call returns; output arrays are caller-
+ *              allocated with the stated length.  The library allocates and
+ *              frees its own device memory; nothing it returns needs freeing
+ *              except the context (gl_destroy).
+ *   errors     0 on success, a negative GL_ERR_* code otherwise; nothing
+ *              throws across the ABI.  gl_last_error() gives a message for the
+ *              calling thread's last failure.  A context is not thread-safe;
+ *              separate contexts are independent.
+ *   streams    all GPU work of a context runs on the stream given to
+ *              gl_create (0 = the legacy default stream).  Calls that return
+ *              results in host memory synchronise that stream.
+ */
+#ifndef GENEO_LAM_H
+#define GENEO_LAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GL_OK = 0,
+    GL_ERR_INVALID_ARG = -1,
+    GL_ERR_OOM = -2,
+    GL_ERR_CUDA = -3,
+    GL_ERR_NOT_SPD = -4,        /* a Cholesky pivot was <= 0 (local or coarse factor) */
+    GL_ERR_NOT_CONVERGED = -5,  /* max_iter reached; info and u still filled */
+    GL_ERR_NAN = -6,            /* a NaN or Inf appeared in the iteration */
+    GL_ERR_TIMEOUT = -7,        /* a device-side wait gave up */
+    GL_ERR_STATE = -8           /* call out of order (e.g. solve before setup) */
+};
+
+enum { GL_PREC_FP64 = 0, GL_PREC_MIXED = 1 };
+
+typedef struct gl_ctx gl_ctx;
+
+/* Orthotropic ply constants (Table 1, Section 2.2).  nu_ij = -eps_j/eps_i
+ * under uniaxial stress along i.  MPa. */
+typedef struct {
+    double E1, E2, E3, G12, G13, G23, nu12, nu13, nu23;
+} gl_ortho;
+
+/* Layered structured mesh (Section 2.2 stacking sequences; Section 3 curved
+ * map x = L + r sin(psi), y = l, z = r cos(psi), psi = arc * t on the arc).
+ *   x[nx+1]  s vertex coordinates: mm for geometry 0 (flat); for geometry 1
+ *            (curved) a parametric t: limb 1 on [-1,0], the arc on [0,1],
+ *            limb 2 on [1,2] (limbs of length limb_L appended tangentially).
+ *   y[ny+1]  width vertex coordinates, mm.
+ *   layers   nlayers layers from the inner (r = R_inner, or z = 0) face out:
+ *            layer_nel[k] elements of equal thickness layer_thick[k]/nel;
+ *            layer_mat[k] indexes the material table (orthotropic entries
+ *            first, then isotropic); layer_angle_deg[k] is the ply angle about
+ *            the laminate normal.
+ *   theta_e  per-element fibre misalignment angle (rad, rotation about the
+ *            width axis l), length nx*ny*nz, or NULL for zero.
+ * Material axes: R = R_l(psi + theta_e) R_r(phi), psi the frame angle at the
+ * element centre (0 on limb 1 and flat plates), C_e constant per element. */
+typedef struct {
+    int nx, ny;
+    const double *x, *y;
+    int nlayers;
+    const int *layer_nel;
+    const double *layer_thick;
+    const int *layer_mat;
+    const double *layer_angle_deg;
+    int geometry;              /* 0 flat, 1 curved */
+    double R_inner, limb_L, arc_deg;
+    const double *theta_e;
+} gl_mesh;
+
+/* Solver options.
+ *   px,py,pz   subdomains per axis (element boxes of near-equal size, the
+ *              first n % p boxes one element larger), grown by `overlap`
+ *              element layers (>= 1) (Section 2.3, Fig. domaindecomp).
+ *   nev        GenEO eigenvectors kept per subdomain (0 = one-level Schwarz).
+ *   max_iter   PCG iteration cap.
+ *   precision  GL_PREC_FP64, or GL_PREC_MIXED (FP32 local factors and solves
+ *              inside FP64 CG, FP64 coarse solve, flexible beta, residual
+ *              replacement every resid_period iterations).
+ *   tol        stop when ||r_k||_2 / ||r_0||_2 <= tol, r_0 = f (x_0 = 0).
+ *   sigma      shift of the definite GenEO pencil (eigenvectors do not
+ *              depend on it); <= 0 selects 1e-3.
+ *   eig_iters  cap on the subspace iterations of the GenEO eigensolver
+ *              (<= 0: 100); it stops earlier once the kept Ritz values of
+ *              every subdomain change by less than 1e-14 (relative). */
+typedef struct {
+    int px, py, pz, overlap, nev, max_iter, precision, resid_period;
+    double tol, sigma;
+    int eig_iters;
+} gl_opts;
+
+/* Results of one solve.  rel_resid_true = ||f - K u||_2 / ||f||_2 on the
+ * free DOFs, recomputed in FP64 after the iteration. */
+typedef struct {
+    int iters;
+    int status;
+    double rel_resid;        /* last recurrence residual ratio */
+    double rel_resid_true;
+    double ms_setup, ms_solve;
+    int64_t n_free;
+    int n_coarse;            /* coarse-space dimension sum_j m_j */
+    int64_t factor_nnz;      /* stored entries of all local factors */
+} gl_info;
+
+/* Context on CUDA device `device`; `cuda_stream` is a cudaStream_t (or NULL). */
+int gl_create(gl_ctx **out, int device, void *cuda_stream);
+void gl_destroy(gl_ctx *ctx);
+const char *gl_strerror(int code);
+const char *gl_last_error(void);
+
+/* Material table: n_ortho orthotropic entries, then n_iso isotropic (E, nu)
+ * pairs (Table 1, Section 2.2). */
+int gl_set_materials(gl_ctx *ctx, int n_ortho, const gl_ortho *ortho, int n_iso,
+                     const double *E_nu_pairs);
+int gl_set_mesh(gl_ctx *ctx, const gl_mesh *mesh);
+/* Prescribed displacements: n DOF indices (int64) and values (mm). */
+int gl_set_dirichlet(gl_ctx *ctx, int64_t n, const int64_t *dof, const double *val);
+/* Uniform surface traction t[3] (MPa, global axes) on one box face; repeated
+ * calls add up.  Consistent nodal loads by 3x3 face Gauss quadrature. */
+int gl_set_traction(gl_ctx *ctx, int face, const double t[3]);
+
+/* Builds geometry, element stiffness data, the decomposition, the local
+ * nested-dissection supernodal Cholesky factors, the GenEO coarse space and
+ * the coarse Cholesky factor (Section 2.3). */
+int gl_setup(gl_ctx *ctx, const gl_opts *opts);
+
+int gl_num_dofs(const gl_ctx *ctx, int64_t *n_dof);
+int gl_num_elems(const gl_ctx *ctx, int64_t *n_elem);
+/* Assembled load vector f (length N) of the tractions. */
+int gl_rhs(gl_ctx *ctx, double *f);
+
+/* PCG solve of K u = f with the prescribed Dirichlet values.  f has length N
+ * (NULL = the assembled tractions); entries at Dirichlet DOFs are ignored.
+ * u (length N, out) holds the full displacement, prescribed values included.
+ * info may be NULL. */
+int gl_solve(gl_ctx *ctx, const double *f, double *u, gl_info *info);
+
+/* Stress recovery at element centres (Section 2.2 notation): s33 = sigma_rr,
+ * t13 = tau_rs in the local (s, l, r) frame, length nx*ny*nz each (either may
+ * be NULL); peak_s33 (may be NULL) = the maximum of s33 over the isotropic
+ * resin-interface elements. */
+int gl_stress(gl_ctx *ctx, const double *u, double *s33, double *t13, double *peak_s33);
+
+/* Operator pieces, for parity checks against an assembled reference.
+ * gl_apply_K: y = K x over all N DOFs (no Dirichlet elimination), the
+ *   matrix-free element-by-element product of Eq. eq-1.
+ * gl_apply_prec: z = M^{-1} r with M^{-1} = Z K_0^{-1} Z^T + sum_j R_j^T
+ *   A_j^{-1} R_j (Section 2.3); r, z of length N, Dirichlet entries ignored
+ *   on input and zero on output.
+ * gl_geneo_eigenvalues: the kept GenEO eigenvalues, subdomain-major
+ *   (n_sub * nev entries; lambda ascending within a subdomain). */
+int gl_apply_K(gl_ctx *ctx, const double *x, double *y);
+int gl_apply_prec(gl_ctx *ctx, const double *r, double *z);
+int gl_geneo_eigenvalues(gl_ctx *ctx, double *lambda, int capacity, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENEO_LAM_H */

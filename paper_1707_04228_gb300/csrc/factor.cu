@@ -1,0 +1,609 @@
+// Batched multifrontal supernodal Cholesky and triangular solves.
+//
+// Section 2.3 solves each overlapping subdomain problem (zero displacement on
+// the artificial boundary) with a sparse direct method.  Here every subdomain
+// is ordered by geometric nested dissection (symbolic.cpp); the numeric phase
+// walks the dissection trees of all subdomains together, one depth level at a
+// time from the leaves up, so each launch covers every front of that depth in
+// every subdomain:
+//   1. zero the level's dense fronts (f x f, column-major, lower triangle);
+//   2. add the element-matrix entries of the front's pivot columns;
+//   3. extend-add the children's update matrices (child slot 0, then slot 1);
+//   4. blocked right-looking partial Cholesky of the p pivot columns:
+//      diagonal block (POTRF), panel below (TRSM), trailing lower triangle
+//      (SYRK/GEMM) -- the trailing update also forms the update matrix;
+//   5. copy the f x p panel into the factor array.
+// The solves walk the same levels: forward (leaves to root) and backward.
+#include <algorithm>
+#include <cstdio>
+
+#include "factor.h"
+
+namespace gl {
+
+constexpr int NB = 32;        // pivot block
+constexpr int TILE = 64;      // trailing-update tile
+
+// ----------------------------------------------------------------- plan
+
+void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_t s) {
+    P.n_sub = (int)subs.size();
+    P.vec_off.clear();
+    P.vec_len.clear();
+    P.fr.clear();
+    P.levels.clear();
+    P.h_gdof.clear();
+    std::vector<int> rows, rel, pair_elem;
+    std::vector<int16_t> pair_pos;
+    int64_t voff = 0, loff = 0;
+    int max_depth = 0;
+    for (auto &S : subs) max_depth = std::max(max_depth, S.max_depth);
+    P.levels.resize(max_depth + 1);
+    for (int j = 0; j < P.n_sub; ++j) {
+        const SubSymbolic &S = subs[j];
+        P.vec_off.push_back(voff);
+        P.vec_len.push_back(S.n);
+        P.h_gdof.insert(P.h_gdof.end(), S.gdof.begin(), S.gdof.end());
+        int base = (int)P.fr.size();
+        int64_t row_base = (int64_t)rows.size(), rel_base = (int64_t)rel.size(),
+                pair_base = (int64_t)pair_elem.size();
+        for (size_t i = 0; i < S.sn.size(); ++i) {
+            const Supernode &sn = S.sn[i];
+            FrontDesc d{};
+            d.l_off = loff + sn.l_off;
+            d.row_off = row_base + sn.row_off;
+            d.vec_off = voff;
+            d.rel_off = rel_base + sn.rel_off;
+            d.pair_off = pair_base + sn.emap_off;
+            d.p = sn.p;
+            d.q = sn.q;
+            d.n_pairs = sn.n_elem_pairs;
+            d.parent = sn.parent >= 0 ? base + sn.parent : -1;
+            d.sub = j;
+            d.slot = 0;
+            if (sn.parent >= 0) d.slot = (S.sn[sn.parent].child[1] == (int)i) ? 1 : 0;
+            d.first = sn.first;
+            d.vlen = S.n;
+            P.fr.push_back(d);
+            Level &L = P.levels[sn.depth];
+            L.fronts.push_back(base + (int)i);
+            if (sn.parent >= 0) L.child_slot[d.slot].push_back(base + (int)i);
+        }
+        rows.insert(rows.end(), S.rows.begin(), S.rows.end());
+        rel.insert(rel.end(), S.rel.begin(), S.rel.end());
+        pair_elem.insert(pair_elem.end(), S.pair_elem.begin(), S.pair_elem.end());
+        pair_pos.insert(pair_pos.end(), S.pair_pos.begin(), S.pair_pos.end());
+        voff += S.n;
+        loff += S.l_size;
+    }
+    P.n_local = voff;
+    P.l_size = loff;
+    P.ws_max = 0;
+    P.max_f = 0;
+    for (auto &L : P.levels) {
+        int64_t off = 0;
+        for (int g : L.fronts) {
+            FrontDesc &d = P.fr[g];
+            int f = d.p + d.q;
+            d.front_off = off;
+            off += (int64_t)f * f;
+            L.max_p = std::max(L.max_p, d.p);
+            L.max_f = std::max(L.max_f, f);
+        }
+        L.ws = off;
+        P.ws_max = std::max(P.ws_max, off);
+        P.max_f = std::max(P.max_f, L.max_f);
+        std::vector<int> v(L.fronts);
+        L.d_fronts.upload(v, s);
+        L.d_child[0].upload(L.child_slot[0], s);
+        L.d_child[1].upload(L.child_slot[1], s);
+    }
+    P.d_fr.upload(P.fr, s);
+    P.d_rows.upload(rows, s);
+    P.d_rel.upload(rel, s);
+    P.d_pair_elem.upload(pair_elem, s);
+    P.d_pair_pos.upload(pair_pos, s);
+    P.d_gdof.upload(P.h_gdof, s);
+    P.d_vec_off.upload(P.vec_off, s);
+    P.d_vec_len.upload(P.vec_len, s);
+    GL_CUDA(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------------- numeric kernels
+
+template <class T>
+__global__ void k_assemble(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+                           const int *__restrict__ pair_elem, const int16_t *__restrict__ pair_pos,
+                           const int *__restrict__ rows, const double *__restrict__ Ke,
+                           const double *__restrict__ xi, double sigma, T *__restrict__ ws) {
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    const int pr_i = blockIdx.y;
+    if (pr_i >= d.n_pairs) return;
+    const int f = d.p + d.q;
+    const int64_t e = pair_elem[d.pair_off + pr_i];
+    const int16_t *pos = pair_pos + (d.pair_off + pr_i) * 81;
+    __shared__ int16_t sp[81];
+    __shared__ double sx[81];
+    if (threadIdx.x < 81) {
+        int16_t v = pos[threadIdx.x];
+        sp[threadIdx.x] = v;
+        sx[threadIdx.x] = (xi && v >= 0) ? xi[d.vec_off + rows[d.row_off + v]] : 0.0;
+    }
+    __syncthreads();
+    T *F = ws + d.front_off;
+    const double *K = Ke + e * 6561;
+    for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x) {
+        int c = idx / 81, r = idx % 81;    // column (pivot) c, row r
+        int pc = sp[c], pr = sp[r];
+        if (pc < 0 || pc >= d.p || pr < pc) continue;
+        double v = K[81 * r + c];
+        if (sigma != 0.0) v *= 1.0 + sigma * sx[r] * sx[c];
+        atomicAdd(F + pr + (int64_t)pc * f, (T)v);
+    }
+}
+
+template <class T>
+__global__ void k_extend_add(const int *__restrict__ children, const FrontDesc *__restrict__ D,
+                             const int *__restrict__ rel, const T *__restrict__ ws_child, T *__restrict__ ws_par) {
+    const FrontDesc c = D[children[blockIdx.x]];
+    const int qc = c.q;
+    if (qc == 0) return;
+    const FrontDesc par = D[c.parent];
+    const int fc = c.p + c.q, fp = par.p + par.q;
+    const int *rm = rel + c.rel_off;
+    const T *U = ws_child + c.front_off;
+    T *F = ws_par + par.front_off;
+    for (int j = blockIdx.y; j < qc; j += gridDim.y) {
+        const int pj = rm[j];
+        const T *Uc = U + (int64_t)(c.p + j) * fc + c.p;
+        T *Fc = F + (int64_t)pj * fp;
+        for (int i = j + threadIdx.x; i < qc; i += blockDim.x) Fc[rm[i]] += Uc[i];
+    }
+}
+
+// Diagonal block Cholesky (kb <= 32) of each front at pivot offset k0.
+template <class T>
+__global__ void k_potrf(const int *__restrict__ fronts, const FrontDesc *__restrict__ D, T *__restrict__ ws, int k0,
+                        int *__restrict__ err) {
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    if (k0 >= d.p) return;
+    const int kb = min(NB, d.p - k0), f = d.p + d.q;
+    T *A = ws + d.front_off + k0 + (int64_t)k0 * f;
+    __shared__ T a[NB][NB + 1];
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int i = idx % kb, j = idx / kb;
+        a[i][j] = i >= j ? A[i + (int64_t)j * f] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        if (threadIdx.x == 0) {
+            T v = a[j][j];
+            if (!(v > T(0))) {
+                atomicExch(err, 1);
+                v = T(1);
+            }
+            a[j][j] = sqrt(v);
+        }
+        __syncthreads();
+        T djj = a[j][j];
+        for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) a[i][j] /= djj;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+            int i = idx % kb, k = idx / kb;
+            if (k > j && i >= k) a[i][k] -= a[i][j] * a[k][j];
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int i = idx % kb, j = idx / kb;
+        if (i >= j) A[i + (int64_t)j * f] = a[i][j];
+    }
+}
+
+// Panel below the diagonal block: rows r in [k0+kb, f) <- row * L_kk^{-T}.
+template <class T>
+__global__ void k_trsm(const int *__restrict__ fronts, const FrontDesc *__restrict__ D, T *__restrict__ ws, int k0) {
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    if (k0 >= d.p) return;
+    const int kb = min(NB, d.p - k0), f = d.p + d.q;
+    const int r = k0 + kb + blockIdx.y * blockDim.x + threadIdx.x;
+    __shared__ T l[NB][NB + 1];
+    T *F = ws + d.front_off;
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int i = idx % kb, j = idx / kb;
+        l[i][j] = i >= j ? F[(k0 + i) + (int64_t)(k0 + j) * f] : T(0);
+    }
+    __syncthreads();
+    if (r >= f) return;
+    T x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < kb) x[j] = F[r + (int64_t)(k0 + j) * f];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < kb) {
+            T v = x[j];
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+                if (i < j) v -= x[i] * l[j][i];
+            x[j] = v / l[j][j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < kb) F[r + (int64_t)(k0 + j) * f] = x[j];
+}
+
+// Trailing update of the lower triangle: F[r, c] -= sum_j P[r, j] P[c, j] for
+// r >= c >= k0+kb, P the panel columns k0..k0+kb.  64x64 tiles, 256 threads.
+template <class T>
+__global__ void __launch_bounds__(256) k_syrk(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+                                              T *__restrict__ ws, int k0) {
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    if (k0 >= d.p) return;
+    const int kb = min(NB, d.p - k0), f = d.p + d.q;
+    const int base = k0 + kb, m = f - base;
+    if (m <= 0) return;
+    const int nt = (m + TILE - 1) / TILE;
+    const int t = blockIdx.y;
+    if (t >= nt * (nt + 1) / 2) return;
+    // t -> (ti, tj), ti >= tj, row-major over the lower triangle of tiles
+    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    const int r0 = base + ti * TILE, c0 = base + tj * TILE;
+    T *F = ws + d.front_off;
+    __shared__ T sa[NB][TILE + 1], sb[NB][TILE + 1];
+    for (int idx = threadIdx.x; idx < NB * TILE; idx += blockDim.x) {
+        int i = idx % TILE, j = idx / TILE;
+        int r = r0 + i, c = c0 + i;
+        sa[j][i] = (j < kb && r < f) ? F[r + (int64_t)(k0 + j) * f] : T(0);
+        sb[j][i] = (j < kb && c < f) ? F[c + (int64_t)(k0 + j) * f] : T(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll 8
+    for (int j = 0; j < NB; ++j) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = sa[j][tx + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = sb[j][ty + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int r = r0 + tx + 16 * a, c = c0 + ty + 16 * b;
+            if (r < f && c < f && r >= c) F[r + (int64_t)c * f] -= acc[a][b];
+        }
+}
+
+template <class T>
+__global__ void k_copy_panel(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+                             const T *__restrict__ ws, T *__restrict__ L) {
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    const int f = d.p + d.q;
+    const int64_t n = (int64_t)f * d.p;
+    const T *F = ws + d.front_off;
+    T *out = L + d.l_off;
+    for (int64_t idx = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.y * blockDim.x) {
+        int64_t j = idx / f, i = idx % f;
+        out[idx] = i >= j ? F[i + j * f] : T(0);
+    }
+}
+
+static void partial_cholesky_level(const int *d_fronts, int n_fronts, const FrontDesc *d_fr, int max_p, int max_f,
+                                   void *ws, bool fp32, int *d_err, cudaStream_t s) {
+    for (int k0 = 0; k0 < max_p; k0 += NB) {
+        // upper bounds over the level's fronts (a front's last pivot block may be short)
+        int rows = std::max(1, max_f - k0);
+        int m = max_f - k0;
+        int nt = m > 0 ? (m + TILE - 1) / TILE : 0;
+        int tiles = std::max(1, nt * (nt + 1) / 2);
+        dim3 gt(n_fronts, (rows + 127) / 128), gs(n_fronts, tiles);
+        if (fp32) {
+            k_potrf<float><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k0, d_err);
+            k_trsm<float><<<gt, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k0);
+            k_syrk<float><<<gs, 256, 0, s>>>(d_fronts, d_fr, (float *)ws, k0);
+        } else {
+            k_potrf<double><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (double *)ws, k0, d_err);
+            k_trsm<double><<<gt, 128, 0, s>>>(d_fronts, d_fr, (double *)ws, k0);
+            k_syrk<double><<<gs, 256, 0, s>>>(d_fronts, d_fr, (double *)ws, k0);
+        }
+        GL_CUDA(cudaGetLastError());
+    }
+}
+
+template <class T>
+void numeric_factor(FactorPlan &P, const double *Ke, const double *xi, double sigma, T *L, int *d_err,
+                    cudaStream_t s) {
+    DBuf<T> ws[2];
+    ws[0].alloc(std::max<int64_t>(P.ws_max, 1));
+    ws[1].alloc(std::max<int64_t>(P.ws_max, 1));
+    const int nlev = (int)P.levels.size();
+    for (int dpt = nlev - 1; dpt >= 0; --dpt) {
+        Level &Lv = P.levels[dpt];
+        const int nf = (int)Lv.fronts.size();
+        if (nf == 0) continue;
+        T *W = ws[dpt & 1].p;
+        GL_CUDA(cudaMemsetAsync(W, 0, Lv.ws * sizeof(T), s));
+        int max_pairs = 0;
+        for (int g : Lv.fronts) max_pairs = std::max(max_pairs, P.fr[g].n_pairs);
+        if (max_pairs > 0) {
+            k_assemble<T><<<dim3(nf, max_pairs), 256, 0, s>>>(Lv.d_fronts.p, P.d_fr.p, P.d_pair_elem.p,
+                                                            P.d_pair_pos.p, P.d_rows.p, Ke, xi, sigma, W);
+            GL_CUDA(cudaGetLastError());
+        }
+        if (dpt + 1 < nlev) {
+            Level &Lc = P.levels[dpt + 1];
+            for (int slot = 0; slot < 2; ++slot) {
+                int nc = (int)Lc.child_slot[slot].size();
+                if (!nc) continue;
+                int ycols = std::min(std::max(1, Lc.max_f / 8), 1024);
+                k_extend_add<T><<<dim3(nc, ycols), 128, 0, s>>>(Lc.d_child[slot].p, P.d_fr.p, P.d_rel.p,
+                                                              ws[(dpt + 1) & 1].p, W);
+                GL_CUDA(cudaGetLastError());
+            }
+        }
+        partial_cholesky_level(Lv.d_fronts.p, nf, P.d_fr.p, Lv.max_p, Lv.max_f, W, sizeof(T) == 4, d_err, s);
+        int64_t maxpanel = 0;
+        for (int g : Lv.fronts) maxpanel = std::max<int64_t>(maxpanel, (int64_t)(P.fr[g].p + P.fr[g].q) * P.fr[g].p);
+        int gy = (int)std::min<int64_t>(std::max<int64_t>(1, (maxpanel + 255) / 256), 4096);
+        k_copy_panel<T><<<dim3(nf, gy), 256, 0, s>>>(Lv.d_fronts.p, P.d_fr.p, W, L);
+        GL_CUDA(cudaGetLastError());
+    }
+    GL_CUDA(cudaStreamSynchronize(s));   // workspaces are released on return
+}
+
+template void numeric_factor<double>(FactorPlan &, const double *, const double *, double, double *, int *,
+                                     cudaStream_t);
+template void numeric_factor<float>(FactorPlan &, const double *, const double *, double, float *, int *,
+                                    cudaStream_t);
+
+// ----------------------------------------------------------------- solves
+
+// Forward substitution for the fronts of one level: pivots y = L11^{-1} x_p,
+// then the structure rows x_s -= L21 y (atomic: sibling fronts share rows).
+template <class T, int NR>
+__global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+                                             const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
+                                             int kcols, int c0) {
+    extern __shared__ unsigned char smraw[];
+    T *v = reinterpret_cast<T *>(smraw);
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    const int p = d.p, f = d.p + d.q, n = d.vlen;
+    T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
+    for (int i = threadIdx.x; i < f; i += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[i + r * f] = i < p ? xs[(int64_t)r * n + d.first + i] : T(0);
+    __syncthreads();
+    const T *Lp = L + d.l_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int jb = 0; jb < p; jb += 32) {
+        const int kb = min(32, p - jb);
+        if (warp == 0) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                T val = lane < kb ? v[jb + lane + r * f] : T(0);
+                for (int j = 0; j < kb; ++j) {
+                    T yj = __shfl_sync(0xffffffffu, val, j) / Lp[(jb + j) + (int64_t)(jb + j) * f];
+                    if (lane == j) val = yj;
+                    if (lane > j && lane < kb) val -= Lp[(jb + lane) + (int64_t)(jb + j) * f] * yj;
+                }
+                if (lane < kb) v[jb + lane + r * f] = val;
+            }
+        }
+        __syncthreads();
+        for (int i = jb + kb + threadIdx.x; i < f; i += blockDim.x) {
+            T acc[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] = T(0);
+            for (int j = 0; j < kb; ++j) {
+                T l = Lp[i + (int64_t)(jb + j) * f];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] += l * v[jb + j + r * f];
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[i + r * f] -= acc[r];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < f; i += blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (i < p) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
+            else atomicAdd(xs + (int64_t)r * n + rows[d.row_off + i], v[i + r * f]);
+        }
+    }
+}
+
+// Backward substitution: x_p = L11^{-T} (x_p - L21^T x_s).
+template <class T, int NR>
+__global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+                                             const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
+                                             int kcols, int c0) {
+    extern __shared__ unsigned char smraw[];
+    T *v = reinterpret_cast<T *>(smraw);
+    __shared__ T red[32][NR];
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    const int p = d.p, f = d.p + d.q, n = d.vlen;
+    T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
+    for (int i = threadIdx.x; i < f; i += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            v[i + r * f] = i < p ? xs[(int64_t)r * n + d.first + i] : xs[(int64_t)r * n + rows[d.row_off + i]];
+    __syncthreads();
+    const T *Lp = L + d.l_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (p == 0) return;
+    for (int jb = ((p - 1) / 32) * 32; jb >= 0; jb -= 32) {
+        const int kb = min(32, p - jb);
+        // red[j] = sum_{i >= jb+kb} L[i][jb+j] v[i]; warp w owns columns j = w, w+nw, ...
+        for (int j = warp; j < kb; j += nw) {
+            T acc[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] = T(0);
+            const T *col = Lp + (int64_t)(jb + j) * f;
+            for (int i = jb + kb + lane; i < f; i += 32) {
+                T l = col[i];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] += l * v[i + r * f];
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                T a = acc[r];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) red[j][r] = a;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                T val = lane < kb ? v[jb + lane + r * f] - red[lane][r] : T(0);
+                for (int j = kb - 1; j >= 0; --j) {
+                    T yj = __shfl_sync(0xffffffffu, val, j) / Lp[(jb + j) + (int64_t)(jb + j) * f];
+                    if (lane == j) val = yj;
+                    if (lane < j) val -= Lp[(jb + j) + (int64_t)(jb + lane) * f] * yj;
+                }
+                if (lane < kb) v[jb + lane + r * f] = val;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
+}
+
+template <class T, int NR>
+static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c0, cudaStream_t s) {
+    size_t smem = (size_t)P.max_f * NR * sizeof(T);
+    static bool attr_set = false;
+    if (smem > 48 * 1024 || !attr_set) {
+        GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
+        GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
+        attr_set = true;
+    }
+    const int nlev = (int)P.levels.size();
+    for (int dpt = nlev - 1; dpt >= 0; --dpt) {
+        const Level &Lv = P.levels[dpt];
+        if (Lv.fronts.empty()) continue;
+        size_t sm = (size_t)Lv.max_f * NR * sizeof(T);
+        k_fwd<T, NR><<<(unsigned)Lv.fronts.size(), 256, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+    }
+    for (int dpt = 0; dpt < nlev; ++dpt) {
+        const Level &Lv = P.levels[dpt];
+        if (Lv.fronts.empty()) continue;
+        size_t sm = (size_t)Lv.max_f * NR * sizeof(T);
+        k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), 256, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+    }
+    GL_CUDA(cudaGetLastError());
+}
+
+template <class T>
+void factor_solve(const FactorPlan &P, const T *L, T *x, int kcols, cudaStream_t s) {
+    int nr = (size_t)P.max_f * 4 * sizeof(T) <= 200 * 1024 ? 4 : ((size_t)P.max_f * 2 * sizeof(T) <= 200 * 1024 ? 2 : 1);
+    if ((size_t)P.max_f * sizeof(T) > 200 * 1024) fail(GL_ERR_INVALID_ARG, "factor_solve: front too large");
+    int c0 = 0;
+    while (c0 < kcols) {
+        int left = kcols - c0;
+        if (nr >= 4 && left >= 4) { solve_levels<T, 4>(P, L, x, kcols, c0, s); c0 += 4; }
+        else if (nr >= 2 && left >= 2) { solve_levels<T, 2>(P, L, x, kcols, c0, s); c0 += 2; }
+        else { solve_levels<T, 1>(P, L, x, kcols, c0, s); c0 += 1; }
+    }
+}
+
+template void factor_solve<double>(const FactorPlan &, const double *, double *, int, cudaStream_t);
+template void factor_solve<float>(const FactorPlan &, const float *, float *, int, cudaStream_t);
+
+// ----------------------------------------------------------------- local <-> global
+
+template <class T>
+__global__ void k_gather(int64_t n, const int64_t *__restrict__ gdof, const double *__restrict__ r, T *__restrict__ xl) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) xl[i] = (T)r[gdof[i]];
+}
+
+template <class T>
+__global__ void k_scatter_add(int64_t n, const int64_t *__restrict__ gdof, const T *__restrict__ xl, double *__restrict__ z) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(z + gdof[i], (double)xl[i]);
+}
+
+template <class T>
+void gather_local(const FactorPlan &P, const double *r, T *xl, cudaStream_t s) {
+    if (!P.n_local) return;
+    k_gather<T><<<(unsigned)((P.n_local + 255) / 256), 256, 0, s>>>(P.n_local, P.d_gdof.p, r, xl);
+    GL_CUDA(cudaGetLastError());
+}
+template <class T>
+void scatter_add_local(const FactorPlan &P, const T *xl, double *z, cudaStream_t s) {
+    if (!P.n_local) return;
+    k_scatter_add<T><<<(unsigned)((P.n_local + 255) / 256), 256, 0, s>>>(P.n_local, P.d_gdof.p, xl, z);
+    GL_CUDA(cudaGetLastError());
+}
+template void gather_local<double>(const FactorPlan &, const double *, double *, cudaStream_t);
+template void gather_local<float>(const FactorPlan &, const double *, float *, cudaStream_t);
+template void scatter_add_local<double>(const FactorPlan &, const double *, double *, cudaStream_t);
+template void scatter_add_local<float>(const FactorPlan &, const float *, double *, cudaStream_t);
+
+// ----------------------------------------------------------------- dense (coarse) Cholesky
+
+struct DenseOne {
+    DBuf<FrontDesc> d;
+    DBuf<int> idx, rows;
+    int n = -1;
+    void ensure(int n_, cudaStream_t s) {
+        if (n == n_) return;
+        n = n_;
+        FrontDesc f{};
+        f.p = n;
+        f.q = 0;
+        f.first = 0;
+        f.vlen = n;
+        f.parent = -1;
+        d.upload(std::vector<FrontDesc>{f}, s);
+        idx.upload(std::vector<int>{0}, s);
+        std::vector<int> r(n);
+        for (int i = 0; i < n; ++i) r[i] = i;
+        rows.upload(r, s);
+        GL_CUDA(cudaStreamSynchronize(s));
+    }
+};
+
+static DenseOne &dense_desc() {
+    static thread_local DenseOne D;
+    return D;
+}
+
+void dense_cholesky(double *A, int n, int *d_err, cudaStream_t s) {
+    DenseOne &D = dense_desc();
+    D.ensure(n, s);
+    partial_cholesky_level(D.idx.p, 1, D.d.p, n, n, A, false, d_err, s);
+}
+
+void dense_cholesky_solve(const double *L, int n, double *x, cudaStream_t s) {
+    DenseOne &D = dense_desc();
+    D.ensure(n, s);
+    size_t sm = (size_t)n * sizeof(double);
+    GL_CUDA(cudaFuncSetAttribute(k_fwd<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 48 * 1024)));
+    GL_CUDA(cudaFuncSetAttribute(k_bwd<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 48 * 1024)));
+    k_fwd<double, 1><<<1, 256, sm, s>>>(D.idx.p, D.d.p, L, D.rows.p, x, 1, 0);
+    k_bwd<double, 1><<<1, 256, sm, s>>>(D.idx.p, D.d.p, L, D.rows.p, x, 1, 0);
+    GL_CUDA(cudaGetLastError());
+}
+
+}  // namespace gl

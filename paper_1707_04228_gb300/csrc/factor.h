@@ -1,0 +1,74 @@
+// Batched multifrontal supernodal Cholesky of many subdomain matrices, and the
+// batched triangular solves with the factors (Section 2.3: direct local
+// solves of the overlapping Schwarz preconditioner).
+#pragma once
+
+#include "gl_internal.h"
+
+namespace gl {
+
+// Per supernode, flattened over all subdomains of one plan.
+struct FrontDesc {
+    int64_t l_off;      // f x p column-major panel in the factor array
+    int64_t row_off;    // f local row indices in the row array
+    int64_t front_off;  // front workspace offset (within its level's buffer)
+    int64_t vec_off;    // subdomain local-vector offset
+    int64_t rel_off;    // q entries: position of each structure row in the parent front
+    int64_t pair_off;   // (element, 81 positions) pairs assembling into the front
+    int p, q, n_pairs, parent, sub, slot;   // slot: 0/1 = which child of the parent
+    int first, vlen;    // first pivot's local index; subdomain local length
+};
+
+struct Level {
+    std::vector<int> fronts;      // global supernode indices at this depth
+    std::vector<int> child_slot[2];
+    int max_p = 0, max_f = 0;
+    int64_t ws = 0;               // workspace entries used by the level
+    DBuf<int> d_fronts, d_child[2];
+};
+
+struct FactorPlan {
+    int n_sub = 0;
+    std::vector<int64_t> vec_off, vec_len;   // per subdomain
+    int64_t n_local = 0;                     // total local DOFs
+    std::vector<FrontDesc> fr;
+    std::vector<Level> levels;               // index = depth
+    int64_t l_size = 0;
+    int64_t ws_max = 0;
+    int max_f = 0;
+    // device
+    DBuf<FrontDesc> d_fr;
+    DBuf<int> d_rows, d_rel, d_pair_elem;
+    DBuf<int16_t> d_pair_pos;
+    DBuf<int64_t> d_gdof;                    // local -> global DOF (concatenated)
+    DBuf<int64_t> d_vec_off, d_vec_len;      // per subdomain
+    std::vector<int64_t> h_gdof;
+};
+
+void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_t s);
+
+// Numeric factorisation.  Front entries from the element matrices Ke (81x81
+// per element, FP64) scaled by (1 + sigma xi_i xi_j) (xi indexed by local DOF,
+// may be NULL when sigma == 0).  Factor values of type T.
+template <class T>
+void numeric_factor(FactorPlan &P, const double *Ke, const double *xi, double sigma, T *L, int *d_err,
+                    cudaStream_t s);
+
+// x <- L^{-T} L^{-1} x for local multi-vectors of kcols columns per subdomain,
+// each column of the subdomain's length stored contiguously:
+// x[vec_off*kcols + c*n + i] (kcols = 1: plain concatenated local vectors).
+template <class T>
+void factor_solve(const FactorPlan &P, const T *L, T *x, int kcols, cudaStream_t s);
+
+// local <-> global transfers: xl[i] = (T) r[gdof[i]]; z[gdof[i]] += xl[i]
+template <class T>
+void gather_local(const FactorPlan &P, const double *r, T *xl, cudaStream_t s);
+template <class T>
+void scatter_add_local(const FactorPlan &P, const T *xl, double *z, cudaStream_t s);
+
+// Dense SPD matrix (n x n, column-major lower) factorised in place with the
+// same blocked kernels; solve with it.
+void dense_cholesky(double *A, int n, int *d_err, cudaStream_t s);
+void dense_cholesky_solve(const double *L, int n, double *x, cudaStream_t s);
+
+}  // namespace gl

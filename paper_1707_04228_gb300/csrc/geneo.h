@@ -1,0 +1,67 @@
+// GenEO coarse space, coarse operators and PCG vector kernels (Section 2.3).
+#pragma once
+
+#include "factor.h"
+
+namespace gl {
+
+// Element -> local-index maps of every subdomain (for local products with the
+// element matrices): n_pairs entries of (element id, subdomain, 81 local
+// indices or -1).
+struct LocalElems {
+    int64_t n_pairs = 0;
+    DBuf<int> elem, sub;
+    DBuf<int> loc;   // 81 per pair
+};
+
+// y_s += S (K_s) S x_s for every subdomain s: S = diag(xi) if xi != NULL,
+// K_s = sum of the subdomain's element matrices; x, y multi-vectors of nv
+// columns in the per-subdomain layout of FactorPlan (x[vec_off*nv + v*n + i]).
+void local_K_apply(const FactorPlan &P, const LocalElems &E, const double *Ke, const double *xi, const double *x,
+                   double *y, int nv, cudaStream_t s);
+
+// G_s = A_s^T B_s (k x k per subdomain, row-major k*k block per subdomain), A,
+// B multi-vectors of k columns in the FactorPlan layout.
+void local_gram(const FactorPlan &P, const double *A, const double *B, int k, double *G, cudaStream_t s);
+
+// Per subdomain: solve G_B y = mu G_M y (k x k, G_M SPD), eigenvectors
+// G_M-orthonormal, sorted by mu descending; writes Y (k x k, column a = vector
+// a, row-major [b*k + a]) and mu.
+void small_geneig(int n_sub, int k, const double *GB, const double *GM, double *Y, double *mu, int *d_err,
+                  cudaStream_t s);
+
+// X <- X Y per subdomain (k columns), using tmp of the same size.
+void local_rotate(const FactorPlan &P, double *X, const double *Y, int k, double *tmp, cudaStream_t s);
+
+// Deterministic pseudo-random fill of a multi-vector (splitmix64 hash of the index).
+void fill_random(double *x, int64_t n, uint64_t seed, cudaStream_t s);
+
+// Coarse operators: Z stored per subdomain as n_s x m column-major (FactorPlan
+// layout with nv = m).  c[s*m + a] = sum_i Z_s[i, a] r[gdof_s[i]];
+// z[gdof_s[i]] += sum_a Z_s[i, a] y[s*m + a].
+void coarse_restrict(const FactorPlan &P, const double *Z, int m, const double *r, double *c, cudaStream_t s);
+void coarse_prolong(const FactorPlan &P, const double *Z, int m, const double *y, double *z, cudaStream_t s);
+
+// Scales a multi-vector by xi row-wise: X[:, a] *= xi.
+void scale_rows(const FactorPlan &P, double *X, const double *xi, int k, cudaStream_t s);
+
+// ---------------------------------------------------------------- PCG vector kernels
+struct CGScalars {
+    double rho, rho_new, pq, rr, rz_old, alpha, beta, ff;
+};
+
+// out = sum a_i b_i (deterministic two-stage reduction) written to *out (device).
+void dot(const double *a, const double *b, int64_t n, double *partials, double *out, cudaStream_t s);
+// x += alpha p; r -= alpha q, alpha = S->rho / S->pq; partial sums of r.r -> S->rr
+void cg_update_xr(double *x, double *r, const double *p, const double *q, int64_t n, CGScalars *S,
+                  double *partials, cudaStream_t s);
+// beta = rho_new / rho (or flexible), p = z + beta p, rho = rho_new
+void cg_update_p(double *p, const double *z, int64_t n, CGScalars *S, cudaStream_t s);
+// y[dof[i]] = val (val = 0 or from array)
+void set_entries(double *y, const int64_t *dof, int64_t n, const double *vals, cudaStream_t s);
+// y = a - b
+void sub(double *y, const double *a, const double *b, int64_t n, cudaStream_t s);
+void axpy(double *y, double a, const double *x, int64_t n, cudaStream_t s);
+void max_where(const double *v, const uint8_t *mask, int64_t n, double *out, cudaStream_t s);
+
+}  // namespace gl

@@ -11,3 +11,20 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU oracle test")
+
+
+@pytest.fixture(scope="session")
+def gl_lib():
+    """The built CUDA library (built in-tree on first use; needs nvcc)."""
+    from paper_1707_04228_gb300 import _build, lib
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    return lib.load()
+
+
+@pytest.fixture(scope="session")
+def cuda_ok():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return True
