@@ -325,45 +325,100 @@ static void partial_cholesky_level(const int *d_fronts, int n_fronts, const Fron
     }
 }
 
+// Subdomains are factorised in consecutive groups whose two live levels of
+// dense fronts fit a workspace budget; inside a group every level is one set
+// of batched launches.
 template <class T>
 void numeric_factor(FactorPlan &P, const double *Ke, const double *xi, double sigma, T *L, int *d_err,
                     cudaStream_t s) {
-    DBuf<T> ws[2];
-    ws[0].alloc(std::max<int64_t>(P.ws_max, 1));
-    ws[1].alloc(std::max<int64_t>(P.ws_max, 1));
     const int nlev = (int)P.levels.size();
-    for (int dpt = nlev - 1; dpt >= 0; --dpt) {
-        Level &Lv = P.levels[dpt];
-        const int nf = (int)Lv.fronts.size();
-        if (nf == 0) continue;
-        T *W = ws[dpt & 1].p;
-        GL_CUDA(cudaMemsetAsync(W, 0, Lv.ws * sizeof(T), s));
-        int max_pairs = 0;
-        for (int g : Lv.fronts) max_pairs = std::max(max_pairs, P.fr[g].n_pairs);
-        if (max_pairs > 0) {
-            k_assemble<T><<<dim3(nf, max_pairs), 256, 0, s>>>(Lv.d_fronts.p, P.d_fr.p, P.d_pair_elem.p,
-                                                            P.d_pair_pos.p, P.d_rows.p, Ke, xi, sigma, W);
-            GL_CUDA(cudaGetLastError());
+    const int64_t budget = (int64_t)(6e9 / sizeof(T));   // entries per workspace buffer
+    std::vector<int> depth_of(P.fr.size());
+    for (int d = 0; d < nlev; ++d)
+        for (int g : P.levels[d].fronts) depth_of[g] = d;
+    std::vector<int64_t> sub_ws((size_t)P.n_sub * nlev, 0);
+    for (size_t g = 0; g < P.fr.size(); ++g) {
+        int64_t f = P.fr[g].p + P.fr[g].q;
+        sub_ws[(size_t)P.fr[g].sub * nlev + depth_of[g]] += f * f;
+    }
+    std::vector<int> first_front(P.n_sub + 1, 0);
+    for (size_t g = 0; g < P.fr.size(); ++g) first_front[P.fr[g].sub + 1] = (int)g + 1;
+    for (int j = 1; j <= P.n_sub; ++j) first_front[j] = std::max(first_front[j], first_front[j - 1]);
+    std::vector<FrontDesc> fr = P.fr;
+    DBuf<FrontDesc> d_fr;
+    DBuf<T> ws[2];
+    int j0 = 0;
+    while (j0 < P.n_sub) {
+        // grow the group while every level's total stays within the budget
+        std::vector<int64_t> tot(nlev, 0);
+        int j1 = j0;
+        while (j1 < P.n_sub) {
+            bool ok = true;
+            for (int d = 0; d < nlev; ++d)
+                if (tot[d] + sub_ws[(size_t)j1 * nlev + d] > budget) ok = false;
+            if (!ok && j1 > j0) break;
+            for (int d = 0; d < nlev; ++d) tot[d] += sub_ws[(size_t)j1 * nlev + d];
+            ++j1;
         }
-        if (dpt + 1 < nlev) {
-            Level &Lc = P.levels[dpt + 1];
-            for (int slot = 0; slot < 2; ++slot) {
-                int nc = (int)Lc.child_slot[slot].size();
-                if (!nc) continue;
-                int ycols = std::min(std::max(1, Lc.max_f / 8), 1024);
-                k_extend_add<T><<<dim3(nc, ycols), 128, 0, s>>>(Lc.d_child[slot].p, P.d_fr.p, P.d_rel.p,
-                                                              ws[(dpt + 1) & 1].p, W);
+        // per-level lists of this group's fronts and their workspace offsets
+        std::vector<std::vector<int>> lev(nlev), child[2];
+        child[0].resize(nlev);
+        child[1].resize(nlev);
+        std::vector<int> max_p(nlev, 0), max_f(nlev, 0), max_pairs(nlev, 0);
+        std::vector<int64_t> lev_ws(nlev, 0), max_panel(nlev, 0);
+        for (int g = first_front[j0]; g < first_front[j1]; ++g) {
+            int d = depth_of[g];
+            int f = fr[g].p + fr[g].q;
+            fr[g].front_off = lev_ws[d];
+            lev_ws[d] += (int64_t)f * f;
+            lev[d].push_back(g);
+            if (fr[g].parent >= 0) child[fr[g].slot][d].push_back(g);
+            max_p[d] = std::max(max_p[d], fr[g].p);
+            max_f[d] = std::max(max_f[d], f);
+            max_pairs[d] = std::max(max_pairs[d], fr[g].n_pairs);
+            max_panel[d] = std::max<int64_t>(max_panel[d], (int64_t)f * fr[g].p);
+        }
+        int64_t need = 1;
+        for (int d = 0; d < nlev; ++d) need = std::max(need, lev_ws[d]);
+        if ((int64_t)ws[0].n < need) {
+            ws[0].alloc(need);
+            ws[1].alloc(need);
+        }
+        d_fr.upload(fr, s);
+        std::vector<DBuf<int>> d_lev(nlev), d_ch0(nlev), d_ch1(nlev);
+        for (int d = 0; d < nlev; ++d) {
+            d_lev[d].upload(lev[d], s);
+            d_ch0[d].upload(child[0][d], s);
+            d_ch1[d].upload(child[1][d], s);
+        }
+        for (int dpt = nlev - 1; dpt >= 0; --dpt) {
+            const int nf = (int)lev[dpt].size();
+            if (nf == 0) continue;
+            T *W = ws[dpt & 1].p;
+            GL_CUDA(cudaMemsetAsync(W, 0, lev_ws[dpt] * sizeof(T), s));
+            if (max_pairs[dpt] > 0) {
+                k_assemble<T><<<dim3(nf, max_pairs[dpt]), 256, 0, s>>>(d_lev[dpt].p, d_fr.p, P.d_pair_elem.p,
+                                                                     P.d_pair_pos.p, P.d_rows.p, Ke, xi, sigma, W);
                 GL_CUDA(cudaGetLastError());
             }
+            if (dpt + 1 < nlev) {
+                for (int slot = 0; slot < 2; ++slot) {
+                    int nc = (int)child[slot][dpt + 1].size();
+                    if (!nc) continue;
+                    int ycols = std::min(std::max(1, max_f[dpt + 1] / 8), 1024);
+                    k_extend_add<T><<<dim3(nc, ycols), 128, 0, s>>>(slot ? d_ch1[dpt + 1].p : d_ch0[dpt + 1].p,
+                                                                  d_fr.p, P.d_rel.p, ws[(dpt + 1) & 1].p, W);
+                    GL_CUDA(cudaGetLastError());
+                }
+            }
+            partial_cholesky_level(d_lev[dpt].p, nf, d_fr.p, max_p[dpt], max_f[dpt], W, sizeof(T) == 4, d_err, s);
+            int gy = (int)std::min<int64_t>(std::max<int64_t>(1, (max_panel[dpt] + 255) / 256), 4096);
+            k_copy_panel<T><<<dim3(nf, gy), 256, 0, s>>>(d_lev[dpt].p, d_fr.p, W, L);
+            GL_CUDA(cudaGetLastError());
         }
-        partial_cholesky_level(Lv.d_fronts.p, nf, P.d_fr.p, Lv.max_p, Lv.max_f, W, sizeof(T) == 4, d_err, s);
-        int64_t maxpanel = 0;
-        for (int g : Lv.fronts) maxpanel = std::max<int64_t>(maxpanel, (int64_t)(P.fr[g].p + P.fr[g].q) * P.fr[g].p);
-        int gy = (int)std::min<int64_t>(std::max<int64_t>(1, (maxpanel + 255) / 256), 4096);
-        k_copy_panel<T><<<dim3(nf, gy), 256, 0, s>>>(Lv.d_fronts.p, P.d_fr.p, W, L);
-        GL_CUDA(cudaGetLastError());
+        GL_CUDA(cudaStreamSynchronize(s));   // the group's lists are released at the end of this scope
+        j0 = j1;
     }
-    GL_CUDA(cudaStreamSynchronize(s));   // workspaces are released on return
 }
 
 template void numeric_factor<double>(FactorPlan &, const double *, const double *, double, double *, int *,

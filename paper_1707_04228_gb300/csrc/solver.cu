@@ -587,6 +587,11 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
     c->S.zero(s);
     dot(c->fe.p, c->fe.p, N, c->partials.p, &S->ff, s);
     const double ff = read_scalar(c, &S->ff);
+    if (!std::isfinite(ff)) {
+        GL_CUDA(cudaEventDestroy(e0));
+        GL_CUDA(cudaEventDestroy(e1));
+        fail(GL_ERR_NAN, "non-finite load vector");
+    }
     const bool mixed = c->opts.precision == GL_PREC_MIXED;
     c->x.zero(s);
     GL_CUDA(cudaMemcpyAsync(c->r.p, c->fe.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
