@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""GenEO-PCG throughput on one GB300: PCG DOF-iterations/s at 1e-10 relative residual.
+
+Workload (default): the curved corner-unfolding laminate, 90-degree arc of
+5 mm inner radius with 50 mm limbs, 12 plies [0/90/+45/-45/0/90]s of 0.25 mm
+with 0.02 mm resin interfaces, 4 Q2 elements through every layer, 100
+elements on the arc + 10 per limb, 30 across a 15 mm width: 120 x 30 x 92
+triquadratic hexahedra, 8,159,055 DOF, a Gaussian fibre-misalignment field of
+10 degrees amplitude and 4 mm width at mid-arc, limb 1 clamped and a rigid
+opening rotation of the limb-2 end.  128 overlapping subdomains (32 x 4
+in-plane, full thickness, overlap 1), 10 GenEO eigenvectors each, FP64.
+
+A step = one full PCG solve (to ||r||/||f|| <= 1e-10) of K u = f with the
+device-resident load vector, followed by the stress recovery; the setup
+(geometry, factorisations, GenEO coarse space) runs once before the warm-up
+and is reported as setup_s.  value = free DOFs x PCG iterations / solve time.
+
+--impl reference times the CPU oracle (oracle/), as it stands, on a bounded
+sample of the same laminate family on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG DOF-iterations/s at 1e-10 rel. residual; K*u HBM GB/s vs peak"
+UNIT = "DOF-iterations/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name):
+    from paper_1707_04228_gb300 import inputs
+    if name == "corner":
+        lam = inputs.corner_c1()
+        lam.px, lam.py, lam.pz, lam.nev = 32, 4, 1, 10
+        desc = ("curved_corner_120x30x92_q2: 8,159,055 DOF, 128 subdomains (32x4x1 in-plane, overlap 1), "
+                "10 GenEO eigenvectors each, FP64, tol 1e-10")
+    elif name == "corner_small":
+        lam = inputs.curved_corner(n_arc=24, n_limb=4, n_width=8, nel_layer=1, name="curved_corner_small",
+                                   nsub=(8, 2, 1), nev=10)
+        desc = "curved_corner_32x8x23_q2 (small dry-run case), 16 subdomains, 10 eigenvectors, FP64, tol 1e-10"
+    else:
+        raise SystemExit(f"unknown config {name}")
+    return lam, desc
+
+
+def oracle_sample():
+    """Bounded CPU sample of the same family: a 16x3x23 curved corner (12 plies,
+    1 element per layer), 8 in-plane subdomains, 10 eigenvectors."""
+    from paper_1707_04228_gb300 import inputs
+    lam = inputs.curved_corner(n_arc=12, n_limb=2, n_width=3, nel_layer=1, width=3.0, limb_L=5.0,
+                               name="curved_corner_16x3x23", nsub=(8, 1, 1), nev=10, wrinkle_w=1.0)
+    return lam
+
+
+def run_oracle(steps, warmup, max_seconds=None):
+    """Times the oracle's PCG solve (setup excluded); returns dict."""
+    from oracle import fem, geneo
+    lam = oracle_sample()
+    sysm = fem.System(fem.Mesh(lam))
+    dec = geneo.Decomposition(sysm, lam.px, lam.py, lam.pz, lam.overlap)
+    P = geneo.GenEO(dec, lam.nev)
+    nfree = sysm.free.size
+    for _ in range(warmup):
+        geneo.pcg(sysm.Kff, sysm.ff, P.apply, tol=lam.tol)
+    t_tot, it_tot, done, cpu_tot = 0.0, 0, 0, 0.0
+    for _ in range(steps):
+        t0, c0 = time.perf_counter(), time.process_time()
+        _, it, _ = geneo.pcg(sysm.Kff, sysm.ff, P.apply, tol=lam.tol)
+        t_tot += time.perf_counter() - t0
+        cpu_tot += time.process_time() - c0
+        it_tot += it
+        done += 1
+        if max_seconds and t_tot > max_seconds:
+            break
+    return {"value": nfree * it_tot / t_tot, "unit": UNIT, "cores": max(1, round(cpu_tot / t_tot)), "kind": "oracle",
+            "sample": f"{lam.name}: {nfree} free DOF, {lam.px}x{lam.py}x{lam.pz} subdomains, nev {lam.nev}, "
+                      f"{done} PCG solve(s) of {it_tot // max(done, 1)} iterations, setup excluded; "
+                      f"SciPy SuperLU/sparse; cores = process CPU time / wall time over the timed solves",
+            "ms_per_step": 1e3 * t_tot / done}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="corner")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, local_rank, world = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        lam, desc = workload(args.config)
+        r = run_oracle(args.steps, min(args.warmup, 1), max_seconds=150)
+        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": desc, "reference_sample": r["sample"]},
+                "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1707_04228_gb300 import lib
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    lam, desc = workload(args.config)
+    t0 = time.perf_counter()
+    s = lib.Solver.from_laminate(lam, device=local_rank)
+    setup_s = time.perf_counter() - t0
+    N, NE = s.n_dof, s.n_elem
+    dev = torch.device("cuda", local_rank)
+    f = torch.empty(N, dtype=torch.float64, device=dev)
+    s.rhs(out=f)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    s33 = torch.empty(NE, dtype=torch.float64, device=dev)
+    t13 = torch.empty(NE, dtype=torch.float64, device=dev)
+    info = None
+    for _ in range(args.warmup):
+        _, info = s.solve(f, out=u)
+        s.stress(u, s33, t13)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    launches0 = s.kernel_launches()
+    iters = 0
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            _, info = s.solve(f, out=u)
+            s.stress(u, s33, t13)
+            iters += info["iters"]
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier()
+    launches = s.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    units = info["n_free"] * iters
+    if world > 1:
+        tt = torch.tensor([ms, float(units)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_max, units = mx[0].item(), tt[1].item()
+    value = units / (t_max / 1e3)
+
+    # end to end through the public API with host buffers (pinned f in, u out)
+    f_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    f_h.copy_(f.cpu())
+    u_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    f_np, u_np = f_h.numpy(), u_h.numpy()
+    t1 = time.perf_counter()
+    e_iters = 0
+    for _ in range(max(1, args.steps)):
+        _, inf2 = s.solve(f_np, out=u_np)
+        e_iters += inf2["iters"]
+    e2e_s = time.perf_counter() - t1
+    e2e = {"value": info["n_free"] * e_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+           "d2h_bytes_per_step": 8 * N}
+
+    # phase timing pass (separate from the timed steps)
+    s.profile(True)
+    s.solve(f, out=u)
+    prof = s.profile_read()
+    s.profile(False)
+    hbm, hbm_src = peaks()
+    fe, bpe = prof["factor_entries"], prof["factor_bytes_per_entry"]
+    loc_bytes = 2 * fe * bpe + 6 * prof["local_dofs"] * 8          # factors read twice + local vectors
+    loc_flops = 4 * fe
+    loc_ms = prof["ms_local"] / max(prof["n_local"], 1)
+    ku_bytes = 16 * N + NE * (36 + 270) * 8                         # x in, y out, C_e and Gauss-point J^-1, w|J|
+    ku_flops = NE * 6318 * 2                                        # sum-factorised FMA count per element
+    ku_ms = prof["ms_ku"] / max(prof["n_ku"], 1)
+    per_iter = {"ku_ms": ku_ms, "local_ms": loc_ms, "coarse_ms": prof["ms_coarse"] / max(prof["n_coarse"], 1)}
+    loc_tf = loc_flops / (loc_ms / 1e3) / 1e12
+    fp64 = bpe == 8
+    if fp64:
+        roof = {"bound": "alu", "achieved": loc_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": loc_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "local forward/backward supernodal sweeps (all levels) + gather/scatter",
+                "hbm_gbs": loc_bytes / (loc_ms / 1e3) / 1e9, "hbm_frac": loc_bytes / (loc_ms / 1e3) / 1e9 / hbm,
+                "peak_note": f"FP64 ALU peak derived from 152 SMs x 2 FMA/clk x 2.07 GHz; HBM {hbm} GB/s {hbm_src}"}
+    else:
+        gbs = loc_bytes / (loc_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                "kernel": "local forward/backward supernodal sweeps (all levels) + gather/scatter",
+                "peak_note": f"HBM {hbm_src}"}
+    ku = {"hbm_gbs": ku_bytes / (ku_ms / 1e3) / 1e9, "hbm_frac": ku_bytes / (ku_ms / 1e3) / 1e9 / hbm,
+          "fp64_tflops": ku_flops / (ku_ms / 1e3) / 1e12,
+          "fp64_frac": ku_flops / (ku_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "ms": ku_ms,
+          "bytes_per_launch": ku_bytes, "flops_per_launch": ku_flops}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = run_oracle(3, 1, max_seconds=40)
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / max(args.steps, 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "l2": "inputs larger than L2 (local factors of "
+                           f"{fe * bpe / 1e9:.1f} GB stream every iteration)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roof, "ku": ku, "per_iteration": per_iter, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk.summary(), "gpu_launches": launches, "setup_s": setup_s,
+                "iters_per_solve": iters / max(args.steps, 1), "rel_resid_true": info["rel_resid_true"],
+                "n_free": info["n_free"], "factor_entries": fe, "n_coarse": info["n_coarse"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

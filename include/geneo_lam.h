@@ -177,6 +177,29 @@ int gl_apply_K(gl_ctx *ctx, const double *x, double *y);
 int gl_apply_prec(gl_ctx *ctx, const double *r, double *z);
 int gl_geneo_eigenvalues(gl_ctx *ctx, double *lambda, int capacity, int *count);
 
+/* Measurement.  gl_profile(ctx, 1) switches on CUDA-event timing of the
+ * solve's phases on the context's stream (matrix-free K u; local Schwarz
+ * solves = gather + forward/backward sweeps over all factor levels + scatter;
+ * coarse restrict/solve/prolong) and resets the accumulators; 0 switches it
+ * off.  Timing adds a host wait before each phase is reused.
+ * gl_profile_read returns the accumulators and the sizes that turn them into
+ * bandwidth and flop rates.  gl_kernel_launches returns the number of kernels
+ * this library has launched from gl_solve and the gl_apply_* calls since it
+ * was loaded (process-wide). */
+typedef struct {
+    double ms_ku, ms_local, ms_coarse;
+    int64_t n_ku, n_local, n_coarse;     /* timed calls of each phase */
+    int64_t factor_entries;              /* stored entries of all local factor panels */
+    int64_t local_dofs;                  /* sum of the subdomain sizes */
+    int factor_bytes_per_entry;          /* 8 (FP64) or 4 (mixed) */
+    int factor_levels;                   /* non-empty dissection levels (2 sweeps each) */
+    int64_t n_elem, n_dof;
+    int n_sub, n_coarse_dim;
+} gl_profile_data;
+int gl_profile(gl_ctx *ctx, int enable);
+int gl_profile_read(gl_ctx *ctx, gl_profile_data *out);
+long long gl_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

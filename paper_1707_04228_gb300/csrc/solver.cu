@@ -100,7 +100,20 @@ static void parallel_for(int n, F fn) {
 
 using namespace gl;
 
+namespace {
+std::atomic<long long> g_launches(0);   // kernels launched by gl_solve / gl_apply_* (hot path)
+enum { PH_KU = 0, PH_LOCAL = 1, PH_COARSE = 2, PH_N = 3 };
+struct Prof {
+    bool on = false;
+    cudaEvent_t ev[2 * PH_N] = {};
+    double ms[PH_N] = {0, 0, 0};
+    long long count[PH_N] = {0, 0, 0};
+    int pending[PH_N] = {0, 0, 0};
+};
+}  // namespace
+
 struct gl_ctx {
+    Prof prof;
     int device = 0;
     cudaStream_t stream = 0;
     // materials (host, 36 per entry) and kind
@@ -466,12 +479,48 @@ void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir) {
 
 // ---------------------------------------------------------------- operator pieces
 
-void apply_K(gl_ctx *c, const double *x, double *y) { launch_ku(c->m, c->d_C.p, c->d_geo.p, x, y, c->stream); }
+// Per-phase CUDA-event timing (only when profiling is on).  Each phase keeps
+// one start/stop pair; a pending pair is folded into the totals before reuse.
+void prof_fold(gl_ctx *c, int ph) {
+    Prof &P = c->prof;
+    if (!P.pending[ph]) return;
+    GL_CUDA(cudaEventSynchronize(P.ev[2 * ph + 1]));
+    float ms = 0;
+    GL_CUDA(cudaEventElapsedTime(&ms, P.ev[2 * ph], P.ev[2 * ph + 1]));
+    P.ms[ph] += ms;
+    P.count[ph] += 1;
+    P.pending[ph] = 0;
+}
+void prof_begin(gl_ctx *c, int ph) {
+    if (!c->prof.on) return;
+    prof_fold(c, ph);
+    GL_CUDA(cudaEventRecord(c->prof.ev[2 * ph], c->stream));
+}
+void prof_end(gl_ctx *c, int ph) {
+    if (!c->prof.on) return;
+    GL_CUDA(cudaEventRecord(c->prof.ev[2 * ph + 1], c->stream));
+    c->prof.pending[ph] = 1;
+}
+
+int64_t factor_solve_launches(const FactorPlan &P) {
+    int64_t n = 0;
+    for (auto &L : P.levels)
+        if (!L.fronts.empty()) n += 2;
+    return n;
+}
+
+void apply_K(gl_ctx *c, const double *x, double *y) {
+    prof_begin(c, PH_KU);
+    launch_ku(c->m, c->d_C.p, c->d_geo.p, x, y, c->stream);
+    prof_end(c, PH_KU);
+    g_launches += 1;
+}
 
 // z = M^{-1} r (r zero at Dirichlet DOFs)
 void apply_prec(gl_ctx *c, const double *r, double *z) {
     cudaStream_t s = c->stream;
     GL_CUDA(cudaMemsetAsync(z, 0, c->m.n_dof * sizeof(double), s));
+    prof_begin(c, PH_LOCAL);
     if (c->opts.precision == GL_PREC_MIXED) {
         gather_local<float>(c->PD, r, c->xl32.p, s);
         factor_solve<float>(c->PD, c->LD32.p, c->xl32.p, 1, s);
@@ -481,10 +530,15 @@ void apply_prec(gl_ctx *c, const double *r, double *z) {
         factor_solve<double>(c->PD, c->LD64.p, c->xl64.p, 1, s);
         scatter_add_local<double>(c->PD, c->xl64.p, z, s);
     }
+    prof_end(c, PH_LOCAL);
+    g_launches += 2 + factor_solve_launches(c->PD);
     if (c->n0 > 0) {
+        prof_begin(c, PH_COARSE);
         coarse_restrict(c->PN, c->Z.p, c->m_coarse, r, c->cvec.p, s);
         dense_cholesky_solve(c->L0.p, c->n0, c->cvec.p, s);
         coarse_prolong(c->PN, c->Z.p, c->m_coarse, c->cvec.p, z, s);
+        prof_end(c, PH_COARSE);
+        g_launches += 4;
     }
 }
 
@@ -572,6 +626,7 @@ void prepare_rhs(gl_ctx *c, const double *f) {
     apply_K(c, c->ud.p, c->q.p);
     sub(c->fe.p, c->fe.p, c->q.p, N, s);
     set_entries(c->fe.p, c->d_dir_dof.p, nd, nullptr, s);
+    g_launches += 1 + (nd ? 2 : 0);
 }
 
 void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
@@ -586,6 +641,8 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
     CGScalars *S = c->S.p;
     c->S.zero(s);
     dot(c->fe.p, c->fe.p, N, c->partials.p, &S->ff, s);
+    const int nds = nd ? 1 : 0;   // set_entries launches a kernel only for a non-empty list
+    g_launches += 2;
     const double ff = read_scalar(c, &S->ff);
     if (!std::isfinite(ff)) {
         GL_CUDA(cudaEventDestroy(e0));
@@ -600,6 +657,7 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
     if (ff > 0.0) {
         apply_prec(c, c->r.p, c->z.p);
         dot(c->r.p, c->z.p, N, c->partials.p, &S->rho, s);
+        g_launches += 2;
         GL_CUDA(cudaMemcpyAsync(c->p.p, c->z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
         rel = 1.0;
         for (int it = 1; it <= c->opts.max_iter; ++it) {
@@ -607,6 +665,7 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
             set_entries(c->q.p, c->d_dir_dof.p, nd, nullptr, s);
             dot(c->p.p, c->q.p, N, c->partials.p, &S->pq, s);
             cg_update_xr(c->x.p, c->r.p, c->p.p, c->q.p, N, S, c->partials.p, s);
+            g_launches += nds + 4;
             const double rr = read_scalar(c, &S->rr);
             iters = it;
             if (!std::isfinite(rr)) {
@@ -624,11 +683,16 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
                 apply_K(c, c->x.p, c->q.p);
                 set_entries(c->q.p, c->d_dir_dof.p, nd, nullptr, s);
                 sub(c->r.p, c->fe.p, c->q.p, N, s);
+                g_launches += nds + 1;
             }
-            if (mixed) dot(c->r.p, c->z.p, N, c->partials.p, &S->rz_old, s);   // flexible beta
+            if (mixed) {
+                dot(c->r.p, c->z.p, N, c->partials.p, &S->rz_old, s);   // flexible beta
+                g_launches += 2;
+            }
             apply_prec(c, c->r.p, c->z.p);
             dot(c->r.p, c->z.p, N, c->partials.p, &S->rho_new, s);
             cg_update_p(c->p.p, c->z.p, N, S, s);
+            g_launches += 4;
         }
     }
     // true residual and the full displacement
@@ -638,6 +702,8 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
     dot(c->r.p, c->r.p, N, c->partials.p, &S->rr, s);
     const double rt = read_scalar(c, &S->rr);
     axpy(c->x.p, 1.0, c->ud.p, N, s);
+    g_launches += nds + 4;
+    for (int ph = 0; ph < PH_N; ++ph) prof_fold(c, ph);
     GL_CUDA(cudaEventRecord(e1, s));
     from_device(u, c->x.p, N, s);
     float ms = 0;
@@ -898,6 +964,7 @@ int gl_stress(gl_ctx *c, const double *u, double *s33, double *t13, double *peak
         d33.alloc(m.n_elem);
         d13.alloc(m.n_elem);
         launch_stress(m, c->d_X.p, c->d_C.p, c->d_psi.p, du.p, d33.p, d13.p, s);
+        g_launches += 1 + (peak ? 1 : 0);
         if (s33) from_device(s33, d33.p, m.n_elem, s);
         if (t13) from_device(t13, d13.p, m.n_elem, s);
         if (peak) {
@@ -933,6 +1000,51 @@ int gl_apply_prec(gl_ctx *c, const double *r, double *z) {
         from_device(z, c->z.p, c->m.n_dof, s);
     });
 }
+
+int gl_profile(gl_ctx *c, int enable) {
+    return guard([&] {
+        require_ctx(c);
+        Prof &P = c->prof;
+        if (enable && !P.on)
+            for (auto &e : P.ev) GL_CUDA(cudaEventCreate(&e));
+        if (!enable && P.on) {
+            GL_CUDA(cudaStreamSynchronize(c->stream));
+            for (auto &e : P.ev) cudaEventDestroy(e);
+        }
+        P.on = enable != 0;
+        for (int i = 0; i < PH_N; ++i) {
+            P.ms[i] = 0;
+            P.count[i] = 0;
+            P.pending[i] = 0;
+        }
+    });
+}
+
+int gl_profile_read(gl_ctx *c, gl_profile_data *out) {
+    return guard([&] {
+        require_ctx(c);
+        GL_REQUIRE(out, "null output");
+        for (int ph = 0; ph < PH_N; ++ph) prof_fold(c, ph);
+        out->ms_ku = c->prof.ms[PH_KU];
+        out->ms_local = c->prof.ms[PH_LOCAL];
+        out->ms_coarse = c->prof.ms[PH_COARSE];
+        out->n_ku = c->prof.count[PH_KU];
+        out->n_local = c->prof.count[PH_LOCAL];
+        out->n_coarse = c->prof.count[PH_COARSE];
+        out->factor_entries = c->PD.l_size;
+        out->local_dofs = c->PD.n_local;
+        out->factor_bytes_per_entry = c->opts.precision == GL_PREC_MIXED ? 4 : 8;
+        out->n_elem = c->m.n_elem;
+        out->n_dof = c->m.n_dof;
+        out->n_sub = (int)c->boxes.size();
+        out->n_coarse_dim = c->n0;
+        out->factor_levels = 0;
+        for (auto &L : c->PD.levels)
+            if (!L.fronts.empty()) ++out->factor_levels;
+    });
+}
+
+long long gl_kernel_launches(void) { return g_launches.load(); }
 
 int gl_geneo_eigenvalues(gl_ctx *c, double *lambda, int capacity, int *count) {
     return guard([&] {

@@ -54,6 +54,17 @@ class gl_info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gl_profile_data(C.Structure):
+    _fields_ = [("ms_ku", C.c_double), ("ms_local", C.c_double), ("ms_coarse", C.c_double),
+                ("n_ku", C.c_int64), ("n_local", C.c_int64), ("n_coarse", C.c_int64),
+                ("factor_entries", C.c_int64), ("local_dofs", C.c_int64), ("factor_bytes_per_entry", C.c_int),
+                ("factor_levels", C.c_int), ("n_elem", C.c_int64), ("n_dof", C.c_int64), ("n_sub", C.c_int),
+                ("n_coarse_dim", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "gl_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
@@ -73,6 +84,9 @@ SIGNATURES = {
     "gl_apply_K": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_apply_prec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_geneo_eigenvalues": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "gl_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "gl_profile_read": (C.c_int, [C.c_void_p, C.POINTER(gl_profile_data)]),
+    "gl_kernel_launches": (C.c_longlong, []),
 }
 
 _lib = None
@@ -238,6 +252,17 @@ class Solver:
         out = np.empty(self.n_dof) if out is None else out
         _check(self.lib, self.lib.gl_apply_prec(self.ctx, _ptr(r), _ptr(out)))
         return out
+
+    def profile(self, enable=True):
+        _check(self.lib, self.lib.gl_profile(self.ctx, 1 if enable else 0))
+
+    def profile_read(self):
+        d = gl_profile_data()
+        _check(self.lib, self.lib.gl_profile_read(self.ctx, C.byref(d)))
+        return d.as_dict()
+
+    def kernel_launches(self):
+        return int(self.lib.gl_kernel_launches())
 
     def geneo_eigenvalues(self):
         n = C.c_int()
