@@ -445,16 +445,24 @@ __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, con
     __syncthreads();
     const T *Lp = L + d.l_off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ T dblk[32][33];
     for (int jb = 0; jb < p; jb += 32) {
         const int kb = min(32, p - jb);
+        // stage the diagonal block with coalesced loads (column j contiguous)
+        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+            int i = idx & 31, j = idx >> 5;
+            dblk[i][j] = (i < kb && j < kb && i >= j) ? Lp[(jb + i) + (int64_t)(jb + j) * f] : T(0);
+        }
+        __syncthreads();
         if (warp == 0) {
+            const T inv = lane < kb ? T(1) / dblk[lane][lane] : T(0);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 T val = lane < kb ? v[jb + lane + r * f] : T(0);
                 for (int j = 0; j < kb; ++j) {
-                    T yj = __shfl_sync(0xffffffffu, val, j) / Lp[(jb + j) + (int64_t)(jb + j) * f];
+                    T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, inv, j);
                     if (lane == j) val = yj;
-                    if (lane > j && lane < kb) val -= Lp[(jb + lane) + (int64_t)(jb + j) * f] * yj;
+                    if (lane > j) val -= dblk[lane][j] * yj;
                 }
                 if (lane < kb) v[jb + lane + r * f] = val;
             }
@@ -502,8 +510,13 @@ __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, con
     const T *Lp = L + d.l_off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (p == 0) return;
+    __shared__ T dblk[32][33];
     for (int jb = ((p - 1) / 32) * 32; jb >= 0; jb -= 32) {
         const int kb = min(32, p - jb);
+        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+            int i = idx & 31, j = idx >> 5;
+            dblk[i][j] = (i < kb && j < kb && i >= j) ? Lp[(jb + i) + (int64_t)(jb + j) * f] : T(0);
+        }
         // red[j] = sum_{i >= jb+kb} L[i][jb+j] v[i]; warp w owns columns j = w, w+nw, ...
         for (int j = warp; j < kb; j += nw) {
             T acc[NR];
@@ -525,13 +538,14 @@ __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, con
         }
         __syncthreads();
         if (warp == 0) {
+            const T inv = lane < kb ? T(1) / dblk[lane][lane] : T(0);
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 T val = lane < kb ? v[jb + lane + r * f] - red[lane][r] : T(0);
                 for (int j = kb - 1; j >= 0; --j) {
-                    T yj = __shfl_sync(0xffffffffu, val, j) / Lp[(jb + j) + (int64_t)(jb + j) * f];
+                    T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, inv, j);
                     if (lane == j) val = yj;
-                    if (lane < j) val -= Lp[(jb + j) + (int64_t)(jb + lane) * f] * yj;
+                    if (lane < j) val -= dblk[j][lane] * yj;
                 }
                 if (lane < kb) v[jb + lane + r * f] = val;
             }
