@@ -165,6 +165,29 @@ int gl_solve(gl_ctx *ctx, const double *f, double *u, gl_info *info);
  * resin-interface elements. */
 int gl_stress(gl_ctx *ctx, const double *u, double *s33, double *t13, double *peak_s33);
 
+/* Gradients with respect to the per-element misalignment angles theta_e
+ * (adjoint method; the objective is any function of the centre stresses).
+ *
+ * gl_set_theta: replaces theta_e (length nx*ny*nz, rad).  After gl_setup the
+ *   element stiffness tensors C_e are recomputed at once; the local factors
+ *   and the coarse space built for the previous angles are kept and still
+ *   serve as the (SPD) preconditioner, so later solves use K(theta_new).
+ * gl_stress_vjp: vector-Jacobian product of gl_stress at displacement u (N):
+ *   dJdu (N, may be NULL) = sum_e (w33_e d s33_e/du + w13_e d t13_e/du) and
+ *   dJdtheta (n_elem, may be NULL) = sum of the same weights times the partial
+ *   derivatives of s33_e, t13_e with respect to theta_e at fixed u.  w33, w13
+ *   (n_elem) may be NULL (zero).
+ * gl_adjoint: solves K_ff lambda = (dJdu)_f (lambda = 0 on Dirichlet DOFs) by
+ *   PCG with the setup's preconditioner, then writes
+ *   grad[e] = -lambda_e^T (dK_e/dtheta_e) u_e for every element (n_elem),
+ *   dK_e/dtheta_e = sum_q w_q |J_q| B_q^T (dC_e/dtheta_e) B_q.  The total
+ *   derivative of J is grad + dJdtheta from gl_stress_vjp.  info (may be NULL)
+ *   describes the adjoint solve. */
+int gl_set_theta(gl_ctx *ctx, const double *theta_e);
+int gl_stress_vjp(gl_ctx *ctx, const double *u, const double *w33, const double *w13, double *dJdu,
+                  double *dJdtheta);
+int gl_adjoint(gl_ctx *ctx, const double *u, const double *dJdu, double *grad, gl_info *info);
+
 /* Operator pieces, for parity checks against an assembled reference.
  * gl_apply_K: y = K x over all N DOFs (no Dirichlet elimination), the
  *   matrix-free element-by-element product of Eq. eq-1.

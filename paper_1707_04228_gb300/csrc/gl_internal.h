@@ -153,5 +153,12 @@ void launch_elem_stiffness(int64_t n_elem, const double *C, const double *geo, d
                            cudaStream_t s);
 void launch_stress(const MeshHost &m, const double *X, const double *C, const double *psi,
                    const double *u, double *s33, double *t13, cudaStream_t s);
+void launch_stress_vjp(const MeshHost &m, const double *X, const double *C, const double *psi_x,
+                       const int *layer_of_ez, const int *layer_mat, const double *layer_angle, const double *theta,
+                       const double *matC, const double *u, const double *w33, const double *w13, double *dJdu,
+                       double *dJdth, cudaStream_t s);
+void launch_adjoint_contract(const MeshHost &m, const double *geo, const int *layer_of_ez, const int *layer_mat,
+                             const double *layer_angle, const double *theta, const double *psi_x, const double *matC,
+                             const double *u, const double *lam, double *grad, cudaStream_t s);
 
 }  // namespace gl

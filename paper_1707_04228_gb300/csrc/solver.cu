@@ -101,6 +101,10 @@ static void parallel_for(int n, F fn) {
 using namespace gl;
 
 namespace {
+// Nested dissection stops at regions of at most this many nodes (fewer factor
+// entries than larger leaves on the laminate subdomains: 66M against 83M per
+// 6x9x92-element subdomain at 125).
+constexpr int LEAF_NODES = 64;
 std::atomic<long long> g_launches(0);   // kernels launched by gl_solve / gl_apply_* (hot path)
 enum { PH_KU = 0, PH_LOCAL = 1, PH_COARSE = 2, PH_N = 3 };
 struct Prof {
@@ -200,6 +204,20 @@ void check_err(gl_ctx *c, const char *what) {
     }
 }
 
+// Setup phase timing to stderr when GL_VERBOSE is set (syncs the stream).
+void stamp(gl_ctx *c, const char *what) {
+    static const bool on = std::getenv("GL_VERBOSE") != nullptr;
+    static thread_local std::chrono::steady_clock::time_point last = std::chrono::steady_clock::now();
+    if (!on) return;
+    GL_CUDA(cudaStreamSynchronize(c->stream));
+    auto now = std::chrono::steady_clock::now();
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    std::fprintf(stderr, "[gl] %-34s %9.3f s   device used %.1f GB\n", what,
+                 std::chrono::duration<double>(now - last).count(), (tot - fr) / 1e9);
+    last = now;
+}
+
 // ---------------------------------------------------------------- geometry + material
 
 void build_geometry(gl_ctx *c) {
@@ -267,11 +285,11 @@ void build_boxes(gl_ctx *c) {
 }
 
 // Element -> local index maps of one plan's subdomains.
-void build_local_elems(const gl_ctx *c, const FactorPlan &P, LocalElems &E, cudaStream_t s) {
-    const MeshHost &m = c->m;
+void build_local_elems(const MeshHost &m, const std::vector<SubBox> &boxes, const FactorPlan &P, LocalElems &E,
+                       cudaStream_t s) {
     std::vector<int> elem, sub, loc;
     for (int j = 0; j < P.n_sub; ++j) {
-        const SubBox &b = c->boxes[j];
+        const SubBox &b = boxes[j];
         const int nbx = b.nbox[1] - b.nbox[0] + 1, nby = b.nbox[3] - b.nbox[2] + 1, nbz = b.nbox[5] - b.nbox[4] + 1;
         std::vector<int> map((size_t)nbx * nby * nbz * 3, -1);
         const int64_t off = P.vec_off[j];
@@ -341,7 +359,7 @@ __global__ void __launch_bounds__(256) k_coarse_block(const int64_t *__restrict_
     if (threadIdx.x == 0) K0[(row0 + a) + (int64_t)(col0 + b) * n0] = red[0];
 }
 
-void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir) {
+void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir, const double *Ke_p) {
     const MeshHost &m = c->m;
     cudaStream_t s = c->stream;
     const int nev = c->opts.nev;
@@ -349,9 +367,9 @@ void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir) {
     const int nsub = (int)c->boxes.size();
     // Neumann symbolic: all free DOFs of each closed subdomain
     std::vector<SubSymbolic> syms(nsub);
-    parallel_for(nsub, [&](int j) { build_symbolic(m, c->boxes[j], is_dir, true, 125, syms[j]); });
+    parallel_for(nsub, [&](int j) { build_symbolic(m, c->boxes[j], is_dir, true, LEAF_NODES, syms[j]); });
     build_plan(syms, c->PN, s);
-    syms.clear();
+    stamp(c, "Neumann symbolic");
     FactorPlan &PN = c->PN;
     for (int j = 0; j < nsub; ++j)
         if (PN.vec_len[j] < nev) fail(GL_ERR_INVALID_ARG, "subdomain has fewer DOFs than nev");
@@ -378,78 +396,101 @@ void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir) {
     }
     DBuf<double> d_xi;
     d_xi.upload(xi, s);
-    // element matrices and the Neumann-side factor of A^N + sigma Xi A^N Xi
-    DBuf<double> Ke;
-    Ke.alloc((size_t)m.n_elem * 6561);
-    launch_elem_stiffness(m.n_elem, c->d_C.p, c->d_geo.p, Ke.p, s);
-    DBuf<double> LN;
-    LN.alloc(PN.l_size);
-    numeric_factor<double>(PN, Ke.p, d_xi.p, sigma, LN.p, c->err.p, s);
-    check_err(c, "GenEO shifted Neumann factorisation");
-    LocalElems E;
-    build_local_elems(c, PN, E, s);
-    // block subspace iteration for the largest mu of B p = mu M p
     const int k = std::min(32, std::max(nev + 4, ((2 * nev + 3) / 4) * 4));
     const int64_t nl = PN.n_local;
-    DBuf<double> V, BV, W, BW, tmp, GB, GM, Y, mu;
-    V.alloc(nl * k);
-    BV.alloc(nl * k);
-    BW.alloc(nl * k);
-    tmp.alloc(nl * k);
-    GB.alloc((size_t)nsub * k * k);
-    GM.alloc((size_t)nsub * k * k);
-    Y.alloc((size_t)nsub * k * k);
-    mu.alloc((size_t)nsub * k);
-    fill_random(V.p, nl * k, 0x1707042280000001ull, s);
-    BV.zero(s);
-    local_K_apply(PN, E, Ke.p, d_xi.p, V.p, BV.p, k, s);        // BV = Xi A^N Xi V
-    // stop when the nev wanted Ritz values of every subdomain settle (or the cap)
-    const int iters = c->opts.eig_iters > 0 ? c->opts.eig_iters : 100;
-    std::vector<double> mu_prev((size_t)nsub * k, 0.0), mu_now((size_t)nsub * k);
-    for (int it = 0; it < iters; ++it) {
-        // W = M^{-1} B V (in place in tmp)
-        GL_CUDA(cudaMemcpyAsync(tmp.p, BV.p, sizeof(double) * nl * k, cudaMemcpyDeviceToDevice, s));
-        factor_solve<double>(PN, LN.p, tmp.p, k, s);
-        std::swap(V.p, tmp.p);                                    // V <- W
-        BW.zero(s);
-        local_K_apply(PN, E, Ke.p, d_xi.p, V.p, BW.p, k, s);     // BW = B W
-        local_gram(PN, V.p, BV.p, k, GM.p, s);                    // W^T M W = W^T (B V)
-        local_gram(PN, V.p, BW.p, k, GB.p, s);                    // W^T B W
-        small_geneig(nsub, k, GB.p, GM.p, Y.p, mu.p, c->err.p, s);
-        check_err(c, "GenEO Rayleigh-Ritz");
-        local_rotate(PN, V.p, Y.p, k, tmp.p, s);
-        local_rotate(PN, BW.p, Y.p, k, tmp.p, s);
-        std::swap(BV.p, BW.p);
-        GL_CUDA(cudaMemcpyAsync(mu_now.data(), mu.p, mu_now.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-        GL_CUDA(cudaStreamSynchronize(s));
-        double change = 0.0;
-        for (int j = 0; j < nsub; ++j)
-            for (int a = 0; a < nev; ++a) {
-                double now = mu_now[(size_t)j * k + a], prev = mu_prev[(size_t)j * k + a];
-                change = std::max(change, std::fabs(now - prev) / std::fabs(now));
-            }
-        mu_prev = mu_now;
-        c->eig_iters_done = it + 1;
-        if (it >= 4 && change < 1e-14) break;
-    }
-    std::vector<double> hmu((size_t)nsub * k);
-    GL_CUDA(cudaMemcpyAsync(hmu.data(), mu.p, hmu.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    GL_CUDA(cudaStreamSynchronize(s));
-    c->eig.clear();
-    for (int j = 0; j < nsub; ++j)
-        for (int a = 0; a < nev; ++a) c->eig.push_back(1.0 / hmu[(size_t)j * k + a] - sigma);
-    // Z = Xi p for the nev smallest lambda
     c->m_coarse = nev;
     c->n0 = nsub * nev;
     c->Z.alloc(nl * nev);
-    k_copy_cols<<<dim3(nsub, 64), 256, 0, s>>>(PN.d_vec_off.p, PN.d_vec_len.p, V.p, k, c->Z.p, nev);
-    GL_CUDA(cudaGetLastError());
-    scale_rows(PN, c->Z.p, d_xi.p, nev, s);
+    c->eig.assign((size_t)nsub * nev, 0.0);
+    const int iters = c->opts.eig_iters > 0 ? c->opts.eig_iters : 100;
+    // Groups of subdomains: factor of A^N + sigma Xi A^N Xi and block subspace
+    // iteration for the largest mu of B p = mu M p, one group at a time.
+    const int64_t budget = (int64_t)(40e9 / sizeof(double));   // factor entries per group
+    int j0 = 0, max_its = 0;
+    while (j0 < nsub) {
+        int j1 = j0;
+        int64_t acc = 0;
+        while (j1 < nsub && (j1 == j0 || acc + syms[j1].l_size <= budget)) acc += syms[j1++].l_size;
+        const int ng = j1 - j0;
+        std::vector<SubSymbolic> gs(syms.begin() + j0, syms.begin() + j1);
+        FactorPlan PG;
+        build_plan(gs, PG, s);
+        gs.clear();
+        const int64_t goff = PN.vec_off[j0], gl = PG.n_local;
+        DBuf<double> LN;
+        LN.alloc(PG.l_size);
+        const double *xg = d_xi.p + goff;
+        numeric_factor<double>(PG, Ke_p, xg, sigma, LN.p, c->err.p, s);
+        check_err(c, "GenEO shifted Neumann factorisation");
+        stamp(c, "Neumann factorisation (group)");
+        std::vector<SubBox> gboxes(c->boxes.begin() + j0, c->boxes.begin() + j1);
+        LocalElems E;
+        build_local_elems(m, gboxes, PG, E, s);
+        DBuf<double> V, BV, BW, tmp, GB, GM, Y, mu;
+        V.alloc(gl * k);
+        BV.alloc(gl * k);
+        BW.alloc(gl * k);
+        tmp.alloc(gl * k);
+        GB.alloc((size_t)ng * k * k);
+        GM.alloc((size_t)ng * k * k);
+        Y.alloc((size_t)ng * k * k);
+        mu.alloc((size_t)ng * k);
+        fill_random(V.p, gl * k, 0x1707042280000001ull + (uint64_t)j0, s);
+        BV.zero(s);
+        local_K_apply(PG, E, Ke_p, xg, V.p, BV.p, k, s);          // BV = Xi A^N Xi V
+        std::vector<double> mu_prev((size_t)ng * k, 0.0), mu_now((size_t)ng * k);
+        int it = 0;
+        for (; it < iters; ++it) {
+            // W = M^{-1} B V
+            GL_CUDA(cudaMemcpyAsync(tmp.p, BV.p, sizeof(double) * gl * k, cudaMemcpyDeviceToDevice, s));
+            factor_solve<double>(PG, LN.p, tmp.p, k, s);
+            std::swap(V.p, tmp.p);
+            BW.zero(s);
+            local_K_apply(PG, E, Ke_p, xg, V.p, BW.p, k, s);       // BW = B W
+            local_gram(PG, V.p, BV.p, k, GM.p, s);                  // W^T M W = W^T (B V)
+            local_gram(PG, V.p, BW.p, k, GB.p, s);                  // W^T B W
+            small_geneig(ng, k, GB.p, GM.p, Y.p, mu.p, c->err.p, s);
+            check_err(c, "GenEO Rayleigh-Ritz");
+            local_rotate(PG, V.p, Y.p, k, tmp.p, s);
+            local_rotate(PG, BW.p, Y.p, k, tmp.p, s);
+            std::swap(BV.p, BW.p);
+            GL_CUDA(cudaMemcpyAsync(mu_now.data(), mu.p, mu_now.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            GL_CUDA(cudaStreamSynchronize(s));
+            double change = 0.0;
+            for (int j = 0; j < ng; ++j)
+                for (int a = 0; a < nev; ++a) {
+                    double now = mu_now[(size_t)j * k + a], prev = mu_prev[(size_t)j * k + a];
+                    change = std::max(change, std::fabs(now - prev) / std::fabs(now));
+                }
+            mu_prev = mu_now;
+            if (it >= 4 && change < 1e-14) {
+                ++it;
+                break;
+            }
+        }
+        max_its = std::max(max_its, it);
+        for (int j = 0; j < ng; ++j)
+            for (int a = 0; a < nev; ++a) c->eig[(size_t)(j0 + j) * nev + a] = 1.0 / mu_now[(size_t)j * k + a] - sigma;
+        // Z columns of these subdomains (global Neumann layout, nev columns)
+        for (int j = 0; j < ng; ++j) {
+            const int64_t n = PG.vec_len[j];
+            GL_CUDA(cudaMemcpy2DAsync(c->Z.p + PN.vec_off[j0 + j] * nev, n * sizeof(double), V.p + PG.vec_off[j] * k,
+                                      n * sizeof(double), n * sizeof(double), nev, cudaMemcpyDeviceToDevice, s));
+        }
+        stamp(c, "GenEO subspace iteration (group)");
+        j0 = j1;
+    }
+    c->eig_iters_done = max_its;
+    if (std::getenv("GL_VERBOSE")) std::fprintf(stderr, "[gl] GenEO subspace iterations (max over groups): %d\n", max_its);
+    syms.clear();
+    scale_rows(PN, c->Z.p, d_xi.p, nev, s);                        // Z = Xi p
+    LocalElems E;
+    build_local_elems(m, c->boxes, PN, E, s);
     // K_0 = Z^T K Z: Y_j = A^N_j Z_j, then blocks against overlapping subdomains
     DBuf<double> KZ, G;
     KZ.alloc(nl * nev);
     KZ.zero(s);
-    local_K_apply(PN, E, Ke.p, nullptr, c->Z.p, KZ.p, nev, s);
+    local_K_apply(PN, E, Ke_p, nullptr, c->Z.p, KZ.p, nev, s);
     G.alloc((size_t)m.n_dof * nev);
     G.zero(s);
     const int n0 = c->n0;
@@ -561,35 +602,41 @@ void setup(gl_ctx *c, const gl_opts &o) {
         c->err.alloc(1);
         c->err.zero(s);
     }
+    stamp(c, "start");
     build_geometry(c);
+    stamp(c, "geometry, materials, loads");
     std::vector<uint8_t> is_dir(m.n_dof, 0);
     for (int64_t d : c->dir_dof) is_dir[d] = 1;
     c->n_free = m.n_dof - (int64_t)std::count(is_dir.begin(), is_dir.end(), (uint8_t)1);
     build_boxes(c);
     const int nsub = (int)c->boxes.size();
     std::vector<SubSymbolic> syms(nsub);
-    parallel_for(nsub, [&](int j) { build_symbolic(m, c->boxes[j], is_dir, false, 125, syms[j]); });
+    parallel_for(nsub, [&](int j) { build_symbolic(m, c->boxes[j], is_dir, false, LEAF_NODES, syms[j]); });
     build_plan(syms, c->PD, s);
     syms.clear();
-    {
-        DBuf<double> Ke;
-        Ke.alloc((size_t)m.n_elem * 6561);
-        launch_elem_stiffness(m.n_elem, c->d_C.p, c->d_geo.p, Ke.p, s);
-        if (c->opts.precision == GL_PREC_MIXED) {
-            c->LD64.release();
-            c->LD32.alloc(c->PD.l_size);
-            numeric_factor<float>(c->PD, Ke.p, nullptr, 0.0, c->LD32.p, c->err.p, s);
-        } else {
-            c->LD32.release();
-            c->LD64.alloc(c->PD.l_size);
-            numeric_factor<double>(c->PD, Ke.p, nullptr, 0.0, c->LD64.p, c->err.p, s);
-        }
-        check_err(c, "local Dirichlet factorisation");
+    stamp(c, "Dirichlet symbolic");
+    // element matrices (FP64, 81x81 per element) for the front assembly
+    DBuf<double> Ke;
+    Ke.alloc((size_t)m.n_elem * 6561);
+    launch_elem_stiffness(m.n_elem, c->d_C.p, c->d_geo.p, Ke.p, s);
+    stamp(c, "element matrices");
+    if (c->opts.precision == GL_PREC_MIXED) {
+        c->LD64.release();
+        c->LD32.alloc(c->PD.l_size);
+        numeric_factor<float>(c->PD, Ke.p, nullptr, 0.0, c->LD32.p, c->err.p, s);
+    } else {
+        c->LD32.release();
+        c->LD64.alloc(c->PD.l_size);
+        numeric_factor<double>(c->PD, Ke.p, nullptr, 0.0, c->LD64.p, c->err.p, s);
     }
+    check_err(c, "local Dirichlet factorisation");
+    stamp(c, "Dirichlet factorisation");
     c->n0 = 0;
     c->m_coarse = 0;
     c->eig.clear();
-    if (c->opts.nev > 0) build_geneo(c, is_dir);
+    if (c->opts.nev > 0) build_geneo(c, is_dir, Ke.p);
+    Ke.release();
+    stamp(c, "GenEO coarse space + K0");
     // work vectors
     const int64_t N = m.n_dof;
     for (DBuf<double> *b : {&c->x, &c->r, &c->z, &c->p, &c->q, &c->ud, &c->fe}) b->alloc(N);
@@ -616,20 +663,21 @@ double read_scalar(gl_ctx *c, const double *d) {
 }
 
 // Effective right-hand side fe = f - K u_D on the free DOFs, 0 on Dirichlet DOFs.
-void prepare_rhs(gl_ctx *c, const double *f) {
+void prepare_rhs(gl_ctx *c, const double *f, bool homogeneous) {
     cudaStream_t s = c->stream;
     const int64_t N = c->m.n_dof, nd = (int64_t)c->dir_dof.size();
     if (f) to_device(c->fe.p, f, N, s);
     else GL_CUDA(cudaMemcpyAsync(c->fe.p, c->d_ftrac.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     c->ud.zero(s);
-    set_entries(c->ud.p, c->d_dir_dof.p, nd, c->d_dir_val.p, s);
+    if (!homogeneous) set_entries(c->ud.p, c->d_dir_dof.p, nd, c->d_dir_val.p, s);
     apply_K(c, c->ud.p, c->q.p);
     sub(c->fe.p, c->fe.p, c->q.p, N, s);
     set_entries(c->fe.p, c->d_dir_dof.p, nd, nullptr, s);
     g_launches += 1 + (nd ? 2 : 0);
 }
 
-void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
+// PCG solve of K u = f; homogeneous = zero Dirichlet values (adjoint solves).
+void solve(gl_ctx *c, const double *f, double *u, gl_info *info, bool homogeneous = false) {
     if (!c->ready) fail(GL_ERR_STATE, "gl_solve before gl_setup");
     cudaStream_t s = c->stream;
     const int64_t N = c->m.n_dof, nd = (int64_t)c->dir_dof.size();
@@ -637,7 +685,7 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
     GL_CUDA(cudaEventCreate(&e0));
     GL_CUDA(cudaEventCreate(&e1));
     GL_CUDA(cudaEventRecord(e0, s));
-    prepare_rhs(c, f);
+    prepare_rhs(c, f, homogeneous);
     CGScalars *S = c->S.p;
     c->S.zero(s);
     dot(c->fe.p, c->fe.p, N, c->partials.p, &S->ff, s);
@@ -673,7 +721,17 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
                 break;
             }
             rel = std::sqrt(rr / ff);
-            if (rel <= c->opts.tol) break;
+            if (rel <= c->opts.tol) {
+                // accept only if the FP64 true residual agrees; otherwise replace r and go on
+                apply_K(c, c->x.p, c->q.p);
+                set_entries(c->q.p, c->d_dir_dof.p, nd, nullptr, s);
+                sub(c->r.p, c->fe.p, c->q.p, N, s);
+                dot(c->r.p, c->r.p, N, c->partials.p, &S->rr, s);
+                g_launches += nds + 3;
+                const double rt2 = read_scalar(c, &S->rr);
+                rel = std::sqrt(rt2 / ff);
+                if (rel <= c->opts.tol) break;
+            }
             if (it == c->opts.max_iter) {
                 status = GL_ERR_NOT_CONVERGED;
                 break;
@@ -998,6 +1056,75 @@ int gl_apply_prec(gl_ctx *c, const double *r, double *z) {
         set_entries(c->r.p, c->d_dir_dof.p, (int64_t)c->dir_dof.size(), nullptr, s);
         apply_prec(c, c->r.p, c->z.p);
         from_device(z, c->z.p, c->m.n_dof, s);
+    });
+}
+
+int gl_set_theta(gl_ctx *c, const double *theta_e) {
+    return guard([&] {
+        require_ctx(c);
+        GL_REQUIRE(c->have_mesh, "gl_set_mesh must come first");
+        GL_REQUIRE(theta_e, "null theta");
+        MeshHost &m = c->m;
+        m.theta = fetch(theta_e, m.n_elem);
+        if (c->ready) {
+            // new C_e for K u and the stresses; the factors and the coarse space are kept
+            c->d_theta.upload(m.theta, c->stream);
+            launch_elem_material(m.n_elem, m.nx, m.ny, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_layer_angle.p,
+                                 c->d_theta.p, c->d_psi.p, c->d_matC.p, c->d_C.p, c->stream);
+            GL_CUDA(cudaStreamSynchronize(c->stream));
+        }
+    });
+}
+
+int gl_stress_vjp(gl_ctx *c, const double *u, const double *w33, const double *w13, double *dJdu, double *dJdth) {
+    return guard([&] {
+        require_ctx(c);
+        if (!c->ready) fail(GL_ERR_STATE, "gl_stress_vjp before gl_setup");
+        GL_REQUIRE(u, "null displacement");
+        cudaStream_t s = c->stream;
+        const MeshHost &m = c->m;
+        DBuf<double> du, d33, d13, dgu, dgt;
+        du.alloc(m.n_dof);
+        to_device(du.p, u, m.n_dof, s);
+        if (w33) {
+            d33.alloc(m.n_elem);
+            to_device(d33.p, w33, m.n_elem, s);
+        }
+        if (w13) {
+            d13.alloc(m.n_elem);
+            to_device(d13.p, w13, m.n_elem, s);
+        }
+        if (dJdu) {
+            dgu.alloc(m.n_dof);
+            dgu.zero(s);
+        }
+        if (dJdth) dgt.alloc(m.n_elem);
+        launch_stress_vjp(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_layer_of_ez.p, c->d_layer_mat.p,
+                          c->d_layer_angle.p, c->d_theta.p, c->d_matC.p, du.p, d33.p, d13.p, dgu.p, dgt.p, s);
+        g_launches += 1;
+        if (dJdu) from_device(dJdu, dgu.p, m.n_dof, s);
+        if (dJdth) from_device(dJdth, dgt.p, m.n_elem, s);
+        GL_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int gl_adjoint(gl_ctx *c, const double *u, const double *dJdu, double *grad, gl_info *info) {
+    return guard([&] {
+        require_ctx(c);
+        if (!c->ready) fail(GL_ERR_STATE, "gl_adjoint before gl_setup");
+        GL_REQUIRE(u && dJdu && grad, "null argument");
+        cudaStream_t s = c->stream;
+        const MeshHost &m = c->m;
+        DBuf<double> lam, du, dg;
+        lam.alloc(m.n_dof);
+        solve(c, dJdu, lam.p, info, true);          // K_ff lambda = (dJ/du)_f, lambda = 0 on Dirichlet DOFs
+        du.alloc(m.n_dof);
+        to_device(du.p, u, m.n_dof, s);
+        dg.alloc(m.n_elem);
+        launch_adjoint_contract(m, c->d_geo.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_layer_angle.p,
+                                c->d_theta.p, c->d_psi.p, c->d_matC.p, du.p, lam.p, dg.p, s);
+        g_launches += 1;
+        from_device(grad, dg.p, m.n_elem, s);
     });
 }
 

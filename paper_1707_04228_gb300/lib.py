@@ -84,6 +84,9 @@ SIGNATURES = {
     "gl_apply_K": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_apply_prec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_geneo_eigenvalues": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "gl_set_theta": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gl_stress_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gl_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(gl_info)]),
     "gl_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "gl_profile_read": (C.c_int, [C.c_void_p, C.POINTER(gl_profile_data)]),
     "gl_kernel_launches": (C.c_longlong, []),
@@ -252,6 +255,25 @@ class Solver:
         out = np.empty(self.n_dof) if out is None else out
         _check(self.lib, self.lib.gl_apply_prec(self.ctx, _ptr(r), _ptr(out)))
         return out
+
+    def set_theta(self, theta):
+        t = theta if hasattr(theta, "data_ptr") else np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+        _check(self.lib, self.lib.gl_set_theta(self.ctx, _ptr(t)))
+
+    def stress_vjp(self, u, w33=None, w13=None, dJdu=None, dJdtheta=None, want_u=True, want_theta=True):
+        if want_u and dJdu is None:
+            dJdu = np.empty(self.n_dof)
+        if want_theta and dJdtheta is None:
+            dJdtheta = np.empty(self.n_elem)
+        _check(self.lib, self.lib.gl_stress_vjp(self.ctx, _ptr(u), _ptr(w33), _ptr(w13), _ptr(dJdu),
+                                                _ptr(dJdtheta)))
+        return dJdu, dJdtheta
+
+    def adjoint(self, u, dJdu, grad=None):
+        grad = np.empty(self.n_elem) if grad is None else grad
+        info = gl_info()
+        _check(self.lib, self.lib.gl_adjoint(self.ctx, _ptr(u), _ptr(dJdu), _ptr(grad), C.byref(info)))
+        return grad, info.as_dict()
 
     def profile(self, enable=True):
         _check(self.lib, self.lib.gl_profile(self.ctx, 1 if enable else 0))

@@ -388,3 +388,29 @@ def test_geneo_iterations_flat_while_one_level_grows():
     assert its[1] <= 1.6 * its[0]
     assert its1[1] >= 4 * its1[0]
     assert its[1] * 3 < its1[1]
+
+
+# --------------------------------------------------------------------------- adjoint
+
+
+def test_oracle_adjoint_gradient_matches_central_differences():
+    """The oracle's adjoint dJ/dtheta of J = ||s33||_8 over the arc resin elements
+    agrees with central differences of J (direct solves, h = 1e-6 rad)."""
+    from oracle import adjoint
+    lam = inputs.corner_mini(n_arc=4, n_limb=1, n_width=2, nel_layer=1, angles=(0, 90), limb_L=2.0, width=2.0)
+    mesh = fem.Mesh(lam)
+    tc = 0.5 * (lam.sv[mesh.eijk[:, 0]] + lam.sv[mesh.eijk[:, 0] + 1])
+    mask = mesh.is_resin & (tc > 0) & (tc < 1)
+    J, grad, u = adjoint.gradient(fem.System(mesh), mask, 8)
+    assert J > 0
+    theta0 = mesh.theta.copy()
+    plies = np.nonzero(~mesh.is_resin)[0]
+    picks = plies[np.argsort(-np.abs(grad[plies]))[:3]]
+    h = 1e-6
+    for e in picks:
+        tp, tm = theta0.copy(), theta0.copy()
+        tp[e] += h
+        tm[e] -= h
+        fd = (adjoint.objective_at(lam, tp, mask, 8) - adjoint.objective_at(lam, tm, mask, 8)) / (2 * h)
+        assert abs(fd - grad[e]) <= 1e-6 * np.abs(grad).max()
+    assert np.all(grad[mesh.is_resin & ~mask] == 0.0)
