@@ -468,17 +468,37 @@ __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, con
             }
         }
         __syncthreads();
-        for (int i = jb + kb + threadIdx.x; i < f; i += blockDim.x) {
-            T acc[NR];
+        if (kb == 32) {
+            // full block: issue the row's 32 loads before any arithmetic
+            const T *col0 = Lp + (int64_t)jb * f;
+            for (int i = jb + 32 + threadIdx.x; i < f; i += blockDim.x) {
+                T l[32];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] = T(0);
-            for (int j = 0; j < kb; ++j) {
-                T l = Lp[i + (int64_t)(jb + j) * f];
+                for (int j = 0; j < 32; ++j) l[j] = col0[i + (int64_t)j * f];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] += l * v[jb + j + r * f];
+                for (int r = 0; r < NR; ++r) {
+                    T a0 = T(0), a1 = T(0);
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        a0 += l[j] * v[jb + j + r * f];
+                        a1 += l[j + 1] * v[jb + j + 1 + r * f];
+                    }
+                    v[i + r * f] -= a0 + a1;
+                }
             }
+        } else {
+            for (int i = jb + kb + threadIdx.x; i < f; i += blockDim.x) {
+                T acc[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) v[i + r * f] -= acc[r];
+                for (int r = 0; r < NR; ++r) acc[r] = T(0);
+                for (int j = 0; j < kb; ++j) {
+                    T l = Lp[i + (int64_t)(jb + j) * f];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[r] += l * v[jb + j + r * f];
+                }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) v[i + r * f] -= acc[r];
+            }
         }
         __syncthreads();
     }
@@ -523,7 +543,18 @@ __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, con
 #pragma unroll
             for (int r = 0; r < NR; ++r) acc[r] = T(0);
             const T *col = Lp + (int64_t)(jb + j) * f;
-            for (int i = jb + kb + lane; i < f; i += 32) {
+            int i = jb + kb + lane;
+            // 8 independent loads per lane in flight
+            for (; i + 7 * 32 < f; i += 8 * 32) {
+                T l[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) l[t] = col[i + 32 * t];
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[r] += l[t] * v[i + 32 * t + r * f];
+            }
+            for (; i < f; i += 32) {
                 T l = col[i];
 #pragma unroll
                 for (int r = 0; r < NR; ++r) acc[r] += l * v[i + r * f];
@@ -662,6 +693,67 @@ void dense_cholesky(double *A, int n, int *d_err, cudaStream_t s) {
     DenseOne &D = dense_desc();
     D.ensure(n, s);
     partial_cholesky_level(D.idx.p, 1, D.d.p, n, n, A, false, d_err, s);
+}
+
+// K^{-1} of a dense SPD matrix through the same partial Cholesky: factoring the
+// p = n pivots of the 2n x 2n front [[A, I], [I, 0]] leaves the Schur
+// complement 0 - I A^{-1} I = -A^{-1} in the trailing block.
+__global__ void k_aug_init(const double *__restrict__ A, int n, double *__restrict__ F) {
+    const int64_t m = 2 * (int64_t)n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < m * m; idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx % m, j = idx / m;
+        double v = 0.0;
+        if (i < n && j < n) v = A[i + j * n];
+        else if (j < n && i - n == j) v = 1.0;
+        F[idx] = v;
+    }
+}
+
+__global__ void k_extract_inv(const double *__restrict__ F, int n, double *__restrict__ Ainv) {
+    const int64_t m = 2 * (int64_t)n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx % n, j = idx / n;
+        int64_t a = i > j ? i : j, b = i > j ? j : i;   // lower triangle of the trailing block
+        Ainv[idx] = -F[(n + a) + (n + b) * m];
+    }
+}
+
+void dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s) {
+    DBuf<FrontDesc> d;
+    DBuf<int> idx;
+    FrontDesc f{};
+    f.p = n;
+    f.q = n;
+    f.vlen = 2 * n;
+    f.parent = -1;
+    d.upload(std::vector<FrontDesc>{f}, s);
+    idx.upload(std::vector<int>{0}, s);
+    DBuf<double> F;
+    F.alloc((size_t)4 * n * n);
+    k_aug_init<<<1024, 256, 0, s>>>(A, n, F.p);
+    GL_CUDA(cudaGetLastError());
+    partial_cholesky_level(idx.p, 1, d.p, n, 2 * n, F.p, false, d_err, s);
+    k_extract_inv<<<1024, 256, 0, s>>>(F.p, n, Ainv);
+    GL_CUDA(cudaGetLastError());
+    GL_CUDA(cudaStreamSynchronize(s));
+}
+
+// y = A x for symmetric A (n x n, column-major): warp per output reads column i.
+__global__ void k_symv(const double *__restrict__ A, int n, const double *__restrict__ x, double *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const double *col = A + (int64_t)i * n;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += col[j] * x[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[i] = acc;
+}
+
+void dense_symv(const double *A, int n, const double *x, double *y, cudaStream_t s) {
+    k_symv<<<(n + 7) / 8, 256, 0, s>>>(A, n, x, y);
+    GL_CUDA(cudaGetLastError());
 }
 
 void dense_cholesky_solve(const double *L, int n, double *x, cudaStream_t s) {

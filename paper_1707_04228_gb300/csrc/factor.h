@@ -70,5 +70,9 @@ void scatter_add_local(const FactorPlan &P, const T *xl, double *z, cudaStream_t
 // same blocked kernels; solve with it.
 void dense_cholesky(double *A, int n, int *d_err, cudaStream_t s);
 void dense_cholesky_solve(const double *L, int n, double *x, cudaStream_t s);
+// A^{-1} (n x n, column-major) of a dense SPD A by Cholesky of the front
+// [[A, I], [I, 0]] (Schur complement -A^{-1}); y = A x for symmetric A.
+void dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s);
+void dense_symv(const double *A, int n, const double *x, double *y, cudaStream_t s);
 
 }  // namespace gl
