@@ -56,6 +56,15 @@ def workload(name):
         lam.px, lam.py, lam.pz, lam.nev = 32, 4, 1, 10
         desc = ("curved_corner_120x30x92_q2: 8,159,055 DOF, 128 subdomains (32x4x1 in-plane, overlap 1), "
                 "10 GenEO eigenvectors each, FP64, tol 1e-10")
+    elif name in ("corner_wide", "corner_mixed"):
+        lam = inputs.curved_corner(n_width=45, width=22.5, name="curved_corner_120x45x92")
+        lam.px, lam.py, lam.pz, lam.nev = 32, 4, 1, 10
+        mixed = name == "corner_mixed"
+        lam.precision = 1 if mixed else 0
+        lam.tol = 1e-8 if mixed else 1e-10
+        desc = ("curved_corner_120x45x92_q2: 12,171,705 DOF, 128 subdomains (32x4x1), 10 eigenvectors, "
+                + ("mixed (FP32 local factors and sweeps, FP64 CG/K*u/coarse), tol 1e-8" if mixed
+                   else "FP64, tol 1e-10"))
     elif name == "corner_small":
         lam = inputs.curved_corner(n_arc=24, n_limb=4, n_width=8, nel_layer=1, name="curved_corner_small",
                                    nsub=(8, 2, 1), nev=10)
@@ -193,7 +202,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     lam, desc = workload(args.config)
     t0 = time.perf_counter()
-    s = lib.Solver.from_laminate(lam, device=local_rank)
+    prec = getattr(lam, "precision", 0)
+    s = lib.Solver.from_laminate(lam, device=local_rank, precision=prec, max_iter=5000)
     setup_s = time.perf_counter() - t0
     N, NE = s.n_dof, s.n_elem
     dev = torch.device("cuda", local_rank)
@@ -292,7 +302,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / max(args.steps, 1), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
+                "data": "synthetic",
                 "config": {"workload": desc, "l2": "inputs larger than L2 (local factors of "
                            f"{fe * bpe / 1e9:.1f} GB stream every iteration)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
