@@ -18,6 +18,7 @@
 #include <cstdio>
 
 #include "factor.h"
+#include "q2.cuh"
 
 namespace gl {
 
@@ -111,32 +112,85 @@ void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_
 
 // ----------------------------------------------------------------- numeric kernels
 
+// One block per (front, element): the element stiffness
+// K_e = sum_q w_q |J_q| B_q^T C_e B_q (FP64) is formed in shared memory, then
+// the entries of the front's pivot columns are added into the front.  With
+// sigma != 0 the entry (i, j) is scaled by 1 + sigma xi_i xi_j (the matrix
+// A^N + sigma Xi A^N Xi of the GenEO pencil).
 template <class T>
-__global__ void k_assemble(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
-                           const int *__restrict__ pair_elem, const int16_t *__restrict__ pair_pos,
-                           const int *__restrict__ rows, const double *__restrict__ Ke,
-                           const double *__restrict__ xi, double sigma, T *__restrict__ ws) {
+__global__ void __launch_bounds__(256) k_assemble(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+                                                  const int *__restrict__ pair_elem,
+                                                  const int16_t *__restrict__ pair_pos, const int *__restrict__ rows,
+                                                  const double *__restrict__ C, const double *__restrict__ geo,
+                                                  const double *__restrict__ xi, double sigma, T *__restrict__ ws) {
     const FrontDesc d = D[fronts[blockIdx.x]];
     const int pr_i = blockIdx.y;
     if (pr_i >= d.n_pairs) return;
+    extern __shared__ double sK[];   // 81 x 81
+    __shared__ int16_t sp[81];
+    __shared__ double sx[81];
+    __shared__ double sG[27][3];
+    __shared__ double sCB[6][81];
+    __shared__ double sC[36];
+    __shared__ double sw;
     const int f = d.p + d.q;
     const int64_t e = pair_elem[d.pair_off + pr_i];
     const int16_t *pos = pair_pos + (d.pair_off + pr_i) * 81;
-    __shared__ int16_t sp[81];
-    __shared__ double sx[81];
     if (threadIdx.x < 81) {
         int16_t v = pos[threadIdx.x];
         sp[threadIdx.x] = v;
         sx[threadIdx.x] = (xi && v >= 0) ? xi[d.vec_off + rows[d.row_off + v]] : 0.0;
     }
+    if (threadIdx.x < 36) sC[threadIdx.x] = C[36 * e + threadIdx.x];
+    Q2Tables Tb;
+    Tb.init();
+    double acc[26];
+#pragma unroll
+    for (int i = 0; i < 26; ++i) acc[i] = 0.0;
+    for (int q = 0; q < 27; ++q) {
+        __syncthreads();
+        const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+        const double *g = geo + 10 * (e * 27 + q);
+        if (threadIdx.x < 27) {
+            int a = threadIdx.x, i = a % 3, j = (a / 3) % 3, k = a / 9;
+            double r0 = Tb.D[qx][i] * Tb.N[qy][j] * Tb.N[qz][k];
+            double r1 = Tb.N[qx][i] * Tb.D[qy][j] * Tb.N[qz][k];
+            double r2 = Tb.N[qx][i] * Tb.N[qy][j] * Tb.D[qz][k];
+            for (int dd = 0; dd < 3; ++dd) sG[a][dd] = r0 * g[0 + dd] + r1 * g[3 + dd] + r2 * g[6 + dd];
+        }
+        if (threadIdx.x == 0) sw = g[9];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 6 * 81; idx += blockDim.x) {
+            int I = idx / 81, col = idx % 81, a = col / 3, c = col % 3;
+            double gx = sG[a][0], gy = sG[a][1], gz = sG[a][2], v;
+            if (c == 0) v = sC[6 * I + 0] * gx + sC[6 * I + 4] * gz + sC[6 * I + 5] * gy;
+            else if (c == 1) v = sC[6 * I + 1] * gy + sC[6 * I + 3] * gz + sC[6 * I + 5] * gx;
+            else v = sC[6 * I + 2] * gz + sC[6 * I + 3] * gy + sC[6 * I + 4] * gx;
+            sCB[I][col] = v;
+        }
+        __syncthreads();
+        const double w = sw;
+        int slot = 0;
+        for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x, ++slot) {
+            int r = idx / 81, col = idx % 81, a = r / 3, c = r % 3;
+            double gx = sG[a][0], gy = sG[a][1], gz = sG[a][2], v;
+            if (c == 0) v = gx * sCB[0][col] + gz * sCB[4][col] + gy * sCB[5][col];
+            else if (c == 1) v = gy * sCB[1][col] + gz * sCB[3][col] + gx * sCB[5][col];
+            else v = gz * sCB[2][col] + gy * sCB[3][col] + gx * sCB[4][col];
+            acc[slot] += w * v;
+        }
+    }
+    {
+        int slot = 0;
+        for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x, ++slot) sK[idx] = acc[slot];
+    }
     __syncthreads();
     T *F = ws + d.front_off;
-    const double *K = Ke + e * 6561;
     for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x) {
         int c = idx / 81, r = idx % 81;    // column (pivot) c, row r
         int pc = sp[c], pr = sp[r];
         if (pc < 0 || pc >= d.p || pr < pc) continue;
-        double v = K[81 * r + c];
+        double v = sK[81 * r + c];
         if (sigma != 0.0) v *= 1.0 + sigma * sx[r] * sx[c];
         atomicAdd(F + pr + (int64_t)pc * f, (T)v);
     }
@@ -329,8 +383,13 @@ static void partial_cholesky_level(const int *d_fronts, int n_fronts, const Fron
 // dense fronts fit a workspace budget; inside a group every level is one set
 // of batched launches.
 template <class T>
-void numeric_factor(FactorPlan &P, const double *Ke, const double *xi, double sigma, T *L, int *d_err,
-                    cudaStream_t s) {
+void numeric_factor(FactorPlan &P, const double *C, const double *geo, const double *xi, double sigma, T *L,
+                    int *d_err, cudaStream_t s) {
+    static bool smem_set = false;
+    if (!smem_set) {
+        GL_CUDA(cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 6561 * 8));
+        smem_set = true;
+    }
     const int nlev = (int)P.levels.size();
     const int64_t budget = (int64_t)(6e9 / sizeof(T));   // entries per workspace buffer
     std::vector<int> depth_of(P.fr.size());
@@ -397,8 +456,8 @@ void numeric_factor(FactorPlan &P, const double *Ke, const double *xi, double si
             T *W = ws[dpt & 1].p;
             GL_CUDA(cudaMemsetAsync(W, 0, lev_ws[dpt] * sizeof(T), s));
             if (max_pairs[dpt] > 0) {
-                k_assemble<T><<<dim3(nf, max_pairs[dpt]), 256, 0, s>>>(d_lev[dpt].p, d_fr.p, P.d_pair_elem.p,
-                                                                     P.d_pair_pos.p, P.d_rows.p, Ke, xi, sigma, W);
+                k_assemble<T><<<dim3(nf, max_pairs[dpt]), 256, 6561 * 8, s>>>(
+                    d_lev[dpt].p, d_fr.p, P.d_pair_elem.p, P.d_pair_pos.p, P.d_rows.p, C, geo, xi, sigma, W);
                 GL_CUDA(cudaGetLastError());
             }
             if (dpt + 1 < nlev) {
@@ -421,10 +480,10 @@ void numeric_factor(FactorPlan &P, const double *Ke, const double *xi, double si
     }
 }
 
-template void numeric_factor<double>(FactorPlan &, const double *, const double *, double, double *, int *,
-                                     cudaStream_t);
-template void numeric_factor<float>(FactorPlan &, const double *, const double *, double, float *, int *,
-                                    cudaStream_t);
+template void numeric_factor<double>(FactorPlan &, const double *, const double *, const double *, double, double *,
+                                     int *, cudaStream_t);
+template void numeric_factor<float>(FactorPlan &, const double *, const double *, const double *, double, float *,
+                                    int *, cudaStream_t);
 
 // ----------------------------------------------------------------- solves
 

@@ -47,11 +47,12 @@ struct FactorPlan {
 
 void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_t s);
 
-// Numeric factorisation.  Front entries from the element matrices Ke (81x81
-// per element, FP64) scaled by (1 + sigma xi_i xi_j) (xi indexed by local DOF,
-// may be NULL when sigma == 0).  Factor values of type T.
+// Numeric factorisation.  Front entries from the element matrices, formed on
+// the fly in FP64 from C_e (36 per element) and the Gauss-point geometry (270
+// per element), scaled by (1 + sigma xi_i xi_j) (xi indexed by local DOF, may
+// be NULL when sigma == 0).  Factor values of type T.
 template <class T>
-void numeric_factor(FactorPlan &P, const double *Ke, const double *xi, double sigma, T *L, int *d_err,
+void numeric_factor(FactorPlan &P, const double *C, const double *geo, const double *xi, double sigma, T *L, int *d_err,
                     cudaStream_t s);
 
 // x <- L^{-T} L^{-1} x for local multi-vectors of kcols columns per subdomain,

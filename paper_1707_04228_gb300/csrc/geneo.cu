@@ -14,51 +14,7 @@ namespace gl {
 
 constexpr int NV_MAX = 32;
 
-// ---------------------------------------------------------------- local element products
-
-__global__ void __launch_bounds__(128) k_local_K(const int *__restrict__ elem, const int *__restrict__ sub,
-                                                const int *__restrict__ loc, const int64_t *__restrict__ voff,
-                                                const int64_t *__restrict__ vlen, const double *__restrict__ Ke,
-                                                const double *__restrict__ xi, const double *__restrict__ x,
-                                                double *__restrict__ y, int nv) {
-    const int64_t pi = blockIdx.x;
-    const int64_t e = elem[pi];
-    const int s = sub[pi];
-    __shared__ int sl[81];
-    __shared__ double sxi[81];
-    __shared__ double sx[NV_MAX][81];
-    const int64_t base = voff[s] * nv, n = vlen[s];
-    if (threadIdx.x < 81) {
-        int l = loc[pi * 81 + threadIdx.x];
-        sl[threadIdx.x] = l;
-        sxi[threadIdx.x] = (xi && l >= 0) ? xi[voff[s] + l] : 1.0;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 81 * nv; idx += blockDim.x) {
-        int c = idx % 81, v = idx / 81;
-        int l = sl[c];
-        sx[v][c] = l >= 0 ? x[base + v * n + l] * sxi[c] : 0.0;
-    }
-    __syncthreads();
-    const double *K = Ke + e * 6561;
-    for (int idx = threadIdx.x; idx < 81 * nv; idx += blockDim.x) {
-        int r = idx % 81, v = idx / 81;
-        int l = sl[r];
-        if (l < 0) continue;
-        double acc = 0.0;
-        for (int c = 0; c < 81; ++c) acc += K[c * 81 + r] * sx[v][c];   // K symmetric
-        atomicAdd(y + base + v * n + l, acc * sxi[r]);
-    }
-}
-
-void local_K_apply(const FactorPlan &P, const LocalElems &E, const double *Ke, const double *xi, const double *x,
-                   double *y, int nv, cudaStream_t s) {
-    if (nv > NV_MAX) fail(GL_ERR_INVALID_ARG, "local_K_apply: too many vectors");
-    if (!E.n_pairs) return;
-    k_local_K<<<(unsigned)E.n_pairs, 128, 0, s>>>(E.elem.p, E.sub.p, E.loc.p, P.d_vec_off.p, P.d_vec_len.p, Ke, xi,
-                                                  x, y, nv);
-    GL_CUDA(cudaGetLastError());
-}
+// (local element products: local_K_apply in ku.cu, matrix-free)
 
 // ---------------------------------------------------------------- Gram matrices
 

@@ -15,10 +15,11 @@ struct LocalElems {
 };
 
 // y_s += S (K_s) S x_s for every subdomain s: S = diag(xi) if xi != NULL,
-// K_s = sum of the subdomain's element matrices; x, y multi-vectors of nv
-// columns in the per-subdomain layout of FactorPlan (x[vec_off*nv + v*n + i]).
-void local_K_apply(const FactorPlan &P, const LocalElems &E, const double *Ke, const double *xi, const double *x,
-                   double *y, int nv, cudaStream_t s);
+// K_s = sum of the subdomain's element matrices (applied matrix-free from C_e
+// and the Gauss-point geometry); x, y multi-vectors of nv columns in the
+// per-subdomain layout of FactorPlan (x[vec_off*nv + v*n + i]).
+void local_K_apply(const FactorPlan &P, const LocalElems &E, const double *C, const double *geo, const double *xi,
+                   const double *x, double *y, int nv, cudaStream_t s);
 
 // G_s = A_s^T B_s (k x k per subdomain, row-major k*k block per subdomain), A,
 // B multi-vectors of k columns in the FactorPlan layout.

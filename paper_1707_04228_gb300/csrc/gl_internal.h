@@ -149,8 +149,6 @@ void launch_traction(const MeshHost &m, const double *X, int face, const double 
                      cudaStream_t s);
 void launch_ku(const MeshHost &m, const double *C, const double *geo, const double *x, double *y,
                cudaStream_t s);
-void launch_elem_stiffness(int64_t n_elem, const double *C, const double *geo, double *Ke,
-                           cudaStream_t s);
 void launch_stress(const MeshHost &m, const double *X, const double *C, const double *psi,
                    const double *u, double *s33, double *t13, cudaStream_t s);
 void launch_stress_vjp(const MeshHost &m, const double *X, const double *C, const double *psi_x,

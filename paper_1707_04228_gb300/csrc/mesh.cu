@@ -304,70 +304,4 @@ void launch_stress(const MeshHost &m, const double *X, const double *C, const do
     GL_CUDA(cudaGetLastError());
 }
 
-// ---------------------------------------------------------------- element stiffness (setup)
-
-// Ke[e][81*r + c] = sum_q w_q |J_q| B_q^T C_e B_q, DOF order 3a + comp.
-// One 256-thread block per element; entries split across threads, shape
-// gradients and C B staged in shared memory per Gauss point.
-__global__ void __launch_bounds__(256) k_elem_stiffness(int64_t n_elem, const double *__restrict__ C,
-                                                        const double *__restrict__ geo, double *__restrict__ Ke) {
-    int64_t e = blockIdx.x;
-    if (e >= n_elem) return;
-    __shared__ double sG[27][3];
-    __shared__ double sCB[6][81];
-    __shared__ double sC[36];
-    __shared__ double sw;
-    Q2Tables T;
-    T.init();
-    if (threadIdx.x < 36) sC[threadIdx.x] = C[36 * e + threadIdx.x];
-    double acc[26];
-#pragma unroll
-    for (int i = 0; i < 26; ++i) acc[i] = 0.0;
-    for (int q = 0; q < 27; ++q) {
-        __syncthreads();
-        int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
-        const double *g = geo + 10 * (e * 27 + q);
-        if (threadIdx.x < 27) {
-            int a = threadIdx.x;
-            int i = a % 3, j = (a / 3) % 3, k = a / 9;
-            double r0 = T.D[qx][i] * T.N[qy][j] * T.N[qz][k];
-            double r1 = T.N[qx][i] * T.D[qy][j] * T.N[qz][k];
-            double r2 = T.N[qx][i] * T.N[qy][j] * T.D[qz][k];
-            for (int d = 0; d < 3; ++d) sG[a][d] = r0 * g[0 + d] + r1 * g[3 + d] + r2 * g[6 + d];
-        }
-        if (threadIdx.x == 0) sw = g[9];
-        __syncthreads();
-        // C B: column (a, c) of B has entries gx,gy,gz at the rows listed below.
-        for (int idx = threadIdx.x; idx < 6 * 81; idx += blockDim.x) {
-            int I = idx / 81, col = idx % 81, a = col / 3, c = col % 3;
-            double gx = sG[a][0], gy = sG[a][1], gz = sG[a][2];
-            double v;
-            if (c == 0) v = sC[6 * I + 0] * gx + sC[6 * I + 4] * gz + sC[6 * I + 5] * gy;
-            else if (c == 1) v = sC[6 * I + 1] * gy + sC[6 * I + 3] * gz + sC[6 * I + 5] * gx;
-            else v = sC[6 * I + 2] * gz + sC[6 * I + 3] * gy + sC[6 * I + 4] * gx;
-            sCB[I][col] = v;
-        }
-        __syncthreads();
-        double w = sw;
-        int slot = 0;
-        for (int idx = threadIdx.x; idx < 81 * 81; idx += blockDim.x, ++slot) {
-            int r = idx / 81, col = idx % 81, a = r / 3, c = r % 3;
-            double gx = sG[a][0], gy = sG[a][1], gz = sG[a][2];
-            double v;
-            if (c == 0) v = gx * sCB[0][col] + gz * sCB[4][col] + gy * sCB[5][col];
-            else if (c == 1) v = gy * sCB[1][col] + gz * sCB[3][col] + gx * sCB[5][col];
-            else v = gz * sCB[2][col] + gy * sCB[3][col] + gx * sCB[4][col];
-            acc[slot] += w * v;
-        }
-    }
-    int slot = 0;
-    for (int idx = threadIdx.x; idx < 81 * 81; idx += blockDim.x, ++slot) Ke[e * 6561 + idx] = acc[slot];
-}
-
-void launch_elem_stiffness(int64_t n_elem, const double *C, const double *geo, double *Ke, cudaStream_t s) {
-    if (n_elem == 0) return;
-    k_elem_stiffness<<<(unsigned)n_elem, 256, 0, s>>>(n_elem, C, geo, Ke);
-    GL_CUDA(cudaGetLastError());
-}
-
 }  // namespace gl

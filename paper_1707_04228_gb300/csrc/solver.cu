@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(256) k_coarse_block(const int64_t *__restrict_
     if (threadIdx.x == 0) K0[(row0 + a) + (int64_t)(col0 + b) * n0] = red[0];
 }
 
-void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir, const double *Ke_p) {
+void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir) {
     const MeshHost &m = c->m;
     cudaStream_t s = c->stream;
     const int nev = c->opts.nev;
@@ -421,7 +421,7 @@ void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir, const double *Ke
         DBuf<double> LN;
         LN.alloc(PG.l_size);
         const double *xg = d_xi.p + goff;
-        numeric_factor<double>(PG, Ke_p, xg, sigma, LN.p, c->err.p, s);
+        numeric_factor<double>(PG, c->d_C.p, c->d_geo.p, xg, sigma, LN.p, c->err.p, s);
         check_err(c, "GenEO shifted Neumann factorisation");
         stamp(c, "Neumann factorisation (group)");
         std::vector<SubBox> gboxes(c->boxes.begin() + j0, c->boxes.begin() + j1);
@@ -438,7 +438,7 @@ void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir, const double *Ke
         mu.alloc((size_t)ng * k);
         fill_random(V.p, gl * k, 0x1707042280000001ull + (uint64_t)j0, s);
         BV.zero(s);
-        local_K_apply(PG, E, Ke_p, xg, V.p, BV.p, k, s);          // BV = Xi A^N Xi V
+        local_K_apply(PG, E, c->d_C.p, c->d_geo.p, xg, V.p, BV.p, k, s);          // BV = Xi A^N Xi V
         std::vector<double> mu_prev((size_t)ng * k, 0.0), mu_now((size_t)ng * k);
         int it = 0;
         for (; it < iters; ++it) {
@@ -447,7 +447,7 @@ void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir, const double *Ke
             factor_solve<double>(PG, LN.p, tmp.p, k, s);
             std::swap(V.p, tmp.p);
             BW.zero(s);
-            local_K_apply(PG, E, Ke_p, xg, V.p, BW.p, k, s);       // BW = B W
+            local_K_apply(PG, E, c->d_C.p, c->d_geo.p, xg, V.p, BW.p, k, s);       // BW = B W
             local_gram(PG, V.p, BV.p, k, GM.p, s);                  // W^T M W = W^T (B V)
             local_gram(PG, V.p, BW.p, k, GB.p, s);                  // W^T B W
             small_geneig(ng, k, GB.p, GM.p, Y.p, mu.p, c->err.p, s);
@@ -504,7 +504,7 @@ void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir, const double *Ke
     DBuf<double> KZ, G;
     KZ.alloc(nl * nev);
     KZ.zero(s);
-    local_K_apply(PN, E, Ke_p, nullptr, c->Z.p, KZ.p, nev, s);
+    local_K_apply(PN, E, c->d_C.p, c->d_geo.p, nullptr, c->Z.p, KZ.p, nev, s);
     G.alloc((size_t)m.n_dof * nev);
     G.zero(s);
     const int n0 = c->n0;
@@ -634,27 +634,21 @@ void setup(gl_ctx *c, const gl_opts &o) {
     build_plan(syms, c->PD, s);
     syms.clear();
     stamp(c, "Dirichlet symbolic");
-    // element matrices (FP64, 81x81 per element) for the front assembly
-    DBuf<double> Ke;
-    Ke.alloc((size_t)m.n_elem * 6561);
-    launch_elem_stiffness(m.n_elem, c->d_C.p, c->d_geo.p, Ke.p, s);
-    stamp(c, "element matrices");
     if (c->opts.precision == GL_PREC_MIXED) {
         c->LD64.release();
         c->LD32.alloc(c->PD.l_size);
-        numeric_factor<float>(c->PD, Ke.p, nullptr, 0.0, c->LD32.p, c->err.p, s);
+        numeric_factor<float>(c->PD, c->d_C.p, c->d_geo.p, nullptr, 0.0, c->LD32.p, c->err.p, s);
     } else {
         c->LD32.release();
         c->LD64.alloc(c->PD.l_size);
-        numeric_factor<double>(c->PD, Ke.p, nullptr, 0.0, c->LD64.p, c->err.p, s);
+        numeric_factor<double>(c->PD, c->d_C.p, c->d_geo.p, nullptr, 0.0, c->LD64.p, c->err.p, s);
     }
     check_err(c, "local Dirichlet factorisation");
     stamp(c, "Dirichlet factorisation");
     c->n0 = 0;
     c->m_coarse = 0;
     c->eig.clear();
-    if (c->opts.nev > 0) build_geneo(c, is_dir, Ke.p);
-    Ke.release();
+    if (c->opts.nev > 0) build_geneo(c, is_dir);
     stamp(c, "GenEO coarse space + K0");
     // work vectors
     const int64_t N = m.n_dof;
