@@ -200,6 +200,35 @@ int gl_apply_K(gl_ctx *ctx, const double *x, double *y);
 int gl_apply_prec(gl_ctx *ctx, const double *r, double *z);
 int gl_geneo_eigenvalues(gl_ctx *ctx, double *lambda, int capacity, int *count);
 
+/* Many laminates solved together (the batched form of the method: every
+ * laminate keeps its own decomposition, local factors, GenEO coarse space
+ * and PCG scalars; their vectors are concatenated so that each phase of the
+ * iteration -- K u, the local forward/backward sweeps of all subdomains of
+ * all laminates, the coarse step, the per-laminate reductions -- is one
+ * launch, and one PCG iteration of the whole batch is replayed as a CUDA
+ * graph).  Laminates that converge stop updating; the others go on.
+ *
+ * gl_batch_create: n contexts with materials, mesh, Dirichlet data and
+ *   tractions set (no gl_setup needed); they must live on one device and
+ *   stay alive while the batch exists; their stream is replaced by the
+ *   batch's.  cuda_stream may be NULL (the batch creates a non-blocking
+ *   stream; graph capture cannot use the legacy default stream).
+ * gl_batch_setup: opts as for gl_setup except px, py: <= 0 selects, per
+ *   laminate, the in-plane subdomain grid (px, py, 1) with 8 <= px py <= 64
+ *   that minimises a cost model of one solve (setup flops and per-iteration
+ *   bytes/flops from the symbolic factorisation of a representative
+ *   subdomain); pz is ignored (subdomains span the thickness).
+ * gl_batch_solve: u[i] (length N_i, host or device) receives laminate i's
+ *   displacement; infos (n entries, may be NULL) its iteration count,
+ *   status and residuals.  Returns the worst status.
+ * gl_batch_grid: the (px, py) chosen for every laminate (2n ints). */
+typedef struct gl_batch gl_batch;
+int gl_batch_create(gl_batch **out, int n, gl_ctx *const *items, void *cuda_stream);
+int gl_batch_setup(gl_batch *batch, const gl_opts *opts);
+int gl_batch_solve(gl_batch *batch, double *const *u, gl_info *infos);
+int gl_batch_grid(const gl_batch *batch, int *pxpy);
+void gl_batch_destroy(gl_batch *batch);
+
 /* Measurement.  gl_profile(ctx, 1) switches on CUDA-event timing of the
  * solve's phases on the context's stream (matrix-free K u; local Schwarz
  * solves = gather + forward/backward sweeps over all factor levels + scatter;

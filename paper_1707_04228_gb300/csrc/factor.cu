@@ -649,12 +649,14 @@ __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, con
 
 template <class T, int NR>
 static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c0, cudaStream_t s) {
+    // raise the dynamic shared-memory limit only when a larger front needs it
+    // (never inside a stream capture once the largest plan has been seen)
     size_t smem = (size_t)P.max_f * NR * sizeof(T);
-    static bool attr_set = false;
-    if (smem > 48 * 1024 || !attr_set) {
-        GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
-        GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
-        attr_set = true;
+    static size_t attr_set = 48 * 1024;
+    if (smem > attr_set) {
+        GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = smem;
     }
     const int nlev = (int)P.levels.size();
     for (int dpt = nlev - 1; dpt >= 0; --dpt) {
@@ -719,40 +721,7 @@ template void gather_local<float>(const FactorPlan &, const double *, float *, c
 template void scatter_add_local<double>(const FactorPlan &, const double *, double *, cudaStream_t);
 template void scatter_add_local<float>(const FactorPlan &, const float *, double *, cudaStream_t);
 
-// ----------------------------------------------------------------- dense (coarse) Cholesky
-
-struct DenseOne {
-    DBuf<FrontDesc> d;
-    DBuf<int> idx, rows;
-    int n = -1;
-    void ensure(int n_, cudaStream_t s) {
-        if (n == n_) return;
-        n = n_;
-        FrontDesc f{};
-        f.p = n;
-        f.q = 0;
-        f.first = 0;
-        f.vlen = n;
-        f.parent = -1;
-        d.upload(std::vector<FrontDesc>{f}, s);
-        idx.upload(std::vector<int>{0}, s);
-        std::vector<int> r(n);
-        for (int i = 0; i < n; ++i) r[i] = i;
-        rows.upload(r, s);
-        GL_CUDA(cudaStreamSynchronize(s));
-    }
-};
-
-static DenseOne &dense_desc() {
-    static thread_local DenseOne D;
-    return D;
-}
-
-void dense_cholesky(double *A, int n, int *d_err, cudaStream_t s) {
-    DenseOne &D = dense_desc();
-    D.ensure(n, s);
-    partial_cholesky_level(D.idx.p, 1, D.d.p, n, n, A, false, d_err, s);
-}
+// ----------------------------------------------------------------- dense (coarse) inverse
 
 // K^{-1} of a dense SPD matrix through the same partial Cholesky: factoring the
 // p = n pivots of the 2n x 2n front [[A, I], [I, 0]] leaves the Schur
@@ -815,14 +784,33 @@ void dense_symv(const double *A, int n, const double *x, double *y, cudaStream_t
     GL_CUDA(cudaGetLastError());
 }
 
-void dense_cholesky_solve(const double *L, int n, double *x, cudaStream_t s) {
-    DenseOne &D = dense_desc();
-    D.ensure(n, s);
-    size_t sm = (size_t)n * sizeof(double);
-    GL_CUDA(cudaFuncSetAttribute(k_fwd<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 48 * 1024)));
-    GL_CUDA(cudaFuncSetAttribute(k_bwd<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 48 * 1024)));
-    k_fwd<double, 1><<<1, 256, sm, s>>>(D.idx.p, D.d.p, L, D.rows.p, x, 1, 0);
-    k_bwd<double, 1><<<1, 256, sm, s>>>(D.idx.p, D.d.p, L, D.rows.p, x, 1, 0);
+// Block-diagonal version: for each block b, y[o_b : o_b + n_b] = A_b x[o_b : o_b + n_b],
+// A_b stored column-major at aoff[b]; one warp per output row.
+__global__ void k_symv_blocks(const double *__restrict__ A, const int64_t *__restrict__ aoff,
+                              const int *__restrict__ voff, const int *__restrict__ nb, int nblk,
+                              const double *__restrict__ x, double *__restrict__ y, int total) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= total) return;
+    int lo = 0, hi = nblk - 1;   // block containing this row
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (voff[mid] <= row) lo = mid;
+        else hi = mid - 1;
+    }
+    const int b = lo, n = nb[b], i = row - voff[b];
+    const double *col = A + aoff[b] + (int64_t)i * n;
+    const double *xb = x + voff[b];
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += col[j] * xb[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[row] = acc;
+}
+
+void dense_symv_blocks(const double *A, const int64_t *aoff, const int *voff, const int *nb, int nblk, int total,
+                       const double *x, double *y, cudaStream_t s) {
+    if (total <= 0) return;
+    k_symv_blocks<<<(total + 7) / 8, 256, 0, s>>>(A, aoff, voff, nb, nblk, x, y, total);
     GL_CUDA(cudaGetLastError());
 }
 

@@ -69,8 +69,9 @@ void scatter_add_local(const FactorPlan &P, const T *xl, double *z, cudaStream_t
 
 // Dense SPD matrix (n x n, column-major lower) factorised in place with the
 // same blocked kernels; solve with it.
-void dense_cholesky(double *A, int n, int *d_err, cudaStream_t s);
-void dense_cholesky_solve(const double *L, int n, double *x, cudaStream_t s);
+// Block-diagonal y = A x: block b (n_b rows, vector offset voff[b], matrix at aoff[b]).
+void dense_symv_blocks(const double *A, const int64_t *aoff, const int *voff, const int *nb, int nblk, int total,
+                       const double *x, double *y, cudaStream_t s);
 // A^{-1} (n x n, column-major) of a dense SPD A by Cholesky of the front
 // [[A, I], [I, 0]] (Schur complement -A^{-1}); y = A x for symmetric A.
 void dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s);

@@ -405,6 +405,105 @@ __global__ void k_finish_p(CGScalars *S) {
     S->rho = S->rho_new;
 }
 
+// ---- per-part (segmented) versions for many laminates solved together
+
+__global__ void __launch_bounds__(256) k_seg_dot(const double *__restrict__ a, const double *__restrict__ b,
+                                                 const PartDesc *__restrict__ parts, double *__restrict__ partials) {
+    const PartDesc pd = parts[blockIdx.x];
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < pd.n_dof; i += (int64_t)gridDim.y * blockDim.x)
+        v += a[pd.dof_off + i] * b[pd.dof_off + i];
+    v = block_sum(v);
+    if (threadIdx.x == 0) partials[blockIdx.x * SEG_BLOCKS + blockIdx.y] = v;
+}
+
+__global__ void k_seg_final(const double *__restrict__ partials, double *__restrict__ out) {
+    const int lane = threadIdx.x;   // 64 threads
+    double v = partials[blockIdx.x * SEG_BLOCKS + lane];
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    __shared__ double w[2];
+    if ((lane & 31) == 0) w[lane >> 5] = v;
+    __syncthreads();
+    if (lane == 0) out[blockIdx.x] = w[0] + w[1];
+}
+
+void seg_dot(const double *a, const double *b, const PartDesc *parts, int n, double *partials, double *out,
+             cudaStream_t s) {
+    k_seg_dot<<<dim3(n, SEG_BLOCKS), 256, 0, s>>>(a, b, parts, partials);
+    k_seg_final<<<n, SEG_BLOCKS, 0, s>>>(partials, out);
+    GL_CUDA(cudaGetLastError());
+}
+
+__global__ void __launch_bounds__(256) k_seg_update_xr(double *__restrict__ x, double *__restrict__ r,
+                                                       const double *__restrict__ p, const double *__restrict__ q,
+                                                       const PartDesc *__restrict__ parts, SegScalars S,
+                                                       double *__restrict__ partials) {
+    const int ip = blockIdx.x;
+    const PartDesc pd = parts[ip];
+    const double alpha = S.active[ip] ? S.rho[ip] / S.pq[ip] : 0.0;
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < pd.n_dof; i += (int64_t)gridDim.y * blockDim.x) {
+        const int64_t g = pd.dof_off + i;
+        x[g] += alpha * p[g];
+        const double ri = r[g] - alpha * q[g];
+        r[g] = ri;
+        v += ri * ri;
+    }
+    v = block_sum(v);
+    if (threadIdx.x == 0) partials[ip * SEG_BLOCKS + blockIdx.y] = v;
+}
+
+void seg_update_xr(double *x, double *r, const double *p, const double *q, const PartDesc *parts, int n,
+                   SegScalars S, double *partials, cudaStream_t s) {
+    k_seg_update_xr<<<dim3(n, SEG_BLOCKS), 256, 0, s>>>(x, r, p, q, parts, S, partials);
+    k_seg_final<<<n, SEG_BLOCKS, 0, s>>>(partials, S.rr);
+    GL_CUDA(cudaGetLastError());
+}
+
+__global__ void __launch_bounds__(256) k_seg_update_p(double *__restrict__ p, const double *__restrict__ z,
+                                                      const PartDesc *__restrict__ parts, SegScalars S) {
+    const int ip = blockIdx.x;
+    const PartDesc pd = parts[ip];
+    const double rho = S.rho[ip];
+    const double beta = rho != 0.0 ? (S.rho_new[ip] - S.rz_old[ip]) / rho : 0.0;
+    for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < pd.n_dof; i += (int64_t)gridDim.y * blockDim.x) {
+        const int64_t g = pd.dof_off + i;
+        p[g] = z[g] + beta * p[g];
+    }
+}
+
+__global__ void k_seg_rho(SegScalars S, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) S.rho[i] = S.rho_new[i];
+}
+
+void seg_update_p(double *p, const double *z, const PartDesc *parts, int n, SegScalars S, cudaStream_t s) {
+    k_seg_update_p<<<dim3(n, SEG_BLOCKS), 256, 0, s>>>(p, z, parts, S);
+    k_seg_rho<<<(n + 127) / 128, 128, 0, s>>>(S, n);
+    GL_CUDA(cudaGetLastError());
+}
+
+__global__ void k_seg_check(SegScalars S, int n, double tol2, int max_iter, int *n_active) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !S.active[i]) return;
+    const int it = ++S.iters[i];
+    const double rr = S.rr[i];
+    int a = 1;
+    if (!(rr > tol2 * S.ff[i]) || it >= max_iter) a = 0;   // converged, stalled at max_iter, or NaN
+    S.active[i] = a;
+    if (a) atomicAdd(n_active, 1);
+}
+
+void seg_check(SegScalars S, int n, double tol, int max_iter, int *n_active, cudaStream_t s) {
+    GL_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), s));
+    k_seg_check<<<(n + 127) / 128, 128, 0, s>>>(S, n, tol * tol, max_iter, n_active);
+    GL_CUDA(cudaGetLastError());
+}
+
 void cg_update_p(double *p, const double *z, int64_t n, CGScalars *S, cudaStream_t s) {
     k_update_p<<<RED_BLOCKS, 256, 0, s>>>(p, z, n, S);
     k_finish_p<<<1, 1, 0, s>>>(S);

@@ -54,6 +54,31 @@ void coarse_prolong(const FactorPlan &P, const double *Z, int m, const double *y
 // Scales a multi-vector by xi row-wise: X[:, a] *= xi.
 void scale_rows(const FactorPlan &P, double *X, const double *xi, int k, cudaStream_t s);
 
+// ---------------------------------------------------------------- many laminates at once
+struct PartDesc {
+    int64_t elem_off, dof_off, n_dof;
+    int nx, ny, NX, NY;
+};
+void launch_ku_batch(const PartDesc *d_parts, int n_parts, int64_t n_elem, int64_t n_dof, const double *C,
+                     const double *geo, const double *x, double *y, cudaStream_t s);
+
+// Per-part PCG state (structure of arrays, n parts each).
+struct SegScalars {
+    double *rho, *rho_new, *pq, *rr, *ff, *rz_old;
+    int *active, *iters;
+};
+constexpr int SEG_BLOCKS = 64;
+// out[i] = sum over part i's range of a*b   (partials: n * SEG_BLOCKS)
+void seg_dot(const double *a, const double *b, const PartDesc *parts, int n, double *partials, double *out,
+             cudaStream_t s);
+// x += alpha_i p, r -= alpha_i q (alpha_i = rho_i/pq_i for active parts, else 0); rr_i = r.r
+void seg_update_xr(double *x, double *r, const double *p, const double *q, const PartDesc *parts, int n,
+                   SegScalars S, double *partials, cudaStream_t s);
+// p = z + beta_i p, beta_i = (rho_new_i - rz_old_i) / rho_i; then rho_i = rho_new_i
+void seg_update_p(double *p, const double *z, const PartDesc *parts, int n, SegScalars S, cudaStream_t s);
+// for active parts: iters_i += 1, deactivate when rr_i <= tol^2 ff_i or iters_i >= max_iter; *n_active = count
+void seg_check(SegScalars S, int n, double tol, int max_iter, int *n_active, cudaStream_t s);
+
 // ---------------------------------------------------------------- PCG vector kernels
 struct CGScalars {
     double rho, rho_new, pq, rr, rz_old, alpha, beta, ff;

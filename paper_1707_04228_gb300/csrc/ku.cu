@@ -173,6 +173,58 @@ void launch_ku(const MeshHost &m, const double *C, const double *geo, const doub
     GL_CUDA(cudaGetLastError());
 }
 
+// Many laminates in one launch: elements of all parts are numbered
+// consecutively (part i owns [elem_off[i], elem_off[i+1])), C and geo are
+// indexed by that global id, and part i's DOFs start at dof_off[i] of the
+// concatenated vectors.  Each warp finds its part by binary search.
+__global__ void __launch_bounds__(32 * KU_EPB) k_ku_batch(const PartDesc *__restrict__ parts, int n_parts,
+                                                         int64_t n_elem, const double *__restrict__ C,
+                                                         const double *__restrict__ geo, const double *__restrict__ x,
+                                                         double *__restrict__ y) {
+    __shared__ KuSmem sm[KU_EPB];
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31;
+    const int64_t eg = (int64_t)blockIdx.x * KU_EPB + w;
+    if (eg >= n_elem) return;
+    int lo = 0, hi = n_parts - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (parts[mid].elem_off <= eg) lo = mid;
+        else hi = mid - 1;
+    }
+    const PartDesc pd = parts[lo];
+    const int64_t e = eg - pd.elem_off;
+    KuSmem &s = sm[w];
+    Q2Tables T;
+    T.init();
+    const int ex = (int)(e % pd.nx), ey = (int)((e / pd.nx) % pd.ny), ez = (int)(e / ((int64_t)pd.nx * pd.ny));
+    int64_t dof = 0;
+    if (t < 27) {
+        int64_t node = (int64_t)(2 * ex + t % 3) +
+                       (int64_t)pd.NX * ((2 * ey + (t / 3) % 3) + (int64_t)pd.NY * (2 * ez + t / 9));
+        dof = pd.dof_off + 3 * node;
+        s.U[0][t] = x[dof + 0];
+        s.U[1][t] = x[dof + 1];
+        s.U[2][t] = x[dof + 2];
+    }
+    for (int i = t; i < 36; i += 32) s.C[i] = C[36 * eg + i];
+    __syncwarp();
+    double out[3];
+    ku_core(s, T, t, geo + 270 * eg, out);
+    if (t < 27) {
+        atomicAdd(y + dof + 0, out[0]);
+        atomicAdd(y + dof + 1, out[1]);
+        atomicAdd(y + dof + 2, out[2]);
+    }
+}
+
+void launch_ku_batch(const PartDesc *d_parts, int n_parts, int64_t n_elem, int64_t n_dof, const double *C,
+                     const double *geo, const double *x, double *y, cudaStream_t s) {
+    GL_CUDA(cudaMemsetAsync(y, 0, n_dof * sizeof(double), s));
+    int64_t nb = (n_elem + KU_EPB - 1) / KU_EPB;
+    k_ku_batch<<<(unsigned)nb, 32 * KU_EPB, 0, s>>>(d_parts, n_parts, n_elem, C, geo, x, y);
+    GL_CUDA(cudaGetLastError());
+}
+
 // Subdomain-local products y_s += S K_s S x_s for nv vectors per subdomain
 // (S = diag(xi) or identity), through the element -> local index maps.
 __global__ void __launch_bounds__(32 * KU_EPB) k_local_ku(int64_t n_pairs, const int *__restrict__ elem,

@@ -16,8 +16,7 @@
 #include <mutex>
 #include <thread>
 
-#include "factor.h"
-#include "geneo.h"
+#include "problem.h"
 
 namespace gl {
 
@@ -56,44 +55,6 @@ static void inv6(const double A[36], double X[36]) {
     }
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) X[6 * i + j] = a[i][j + 6];
-}
-
-static std::vector<std::pair<int, int>> split_range(int n, int p) {
-    std::vector<std::pair<int, int>> out;
-    int q = n / p, r = n % p, s = 0;
-    for (int i = 0; i < p; ++i) {
-        int size = q + (i < r ? 1 : 0);
-        out.push_back({s, s + size});
-        s += size;
-    }
-    return out;
-}
-
-template <class F>
-static void parallel_for(int n, F fn) {
-    int nt = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
-    nt = std::min(nt, n);
-    std::atomic<int> next(0);
-    std::vector<std::thread> th;
-    std::vector<Error> errs;
-    std::mutex mu;
-    bool failed = false;
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([&]() {
-            for (;;) {
-                int i = next++;
-                if (i >= n) break;
-                try {
-                    fn(i);
-                } catch (const Error &e) {
-                    std::lock_guard<std::mutex> g(mu);
-                    errs.push_back(e);
-                    failed = true;
-                }
-            }
-        });
-    for (auto &t : th) t.join();
-    if (failed) throw errs.front();
 }
 
 }  // namespace gl
@@ -139,16 +100,12 @@ struct gl_ctx {
     DBuf<double> d_ftrac;
     // solver
     gl_opts opts{};
-    std::vector<SubBox> boxes;
-    FactorPlan PD, PN;
+    Problem prob;        // this laminate as a one-part problem (subdomain boxes, numbering)
+    FactorPlan PD;       // local Dirichlet factors (all subdomains)
     DBuf<double> LD64;
     DBuf<float> LD32;
-    DBuf<double> Z;      // coarse basis, Neumann-local layout, m columns
-    int m_coarse = 0, n0 = 0;
-    DBuf<double> L0;     // K_0 during setup, then K_0^{-1} (dense, from its Cholesky factorisation)
+    Coarse co;           // GenEO coarse space and K_0^{-1}
     DBuf<double> cvec2;
-    std::vector<double> eig;
-    int eig_iters_done = 0;
     // work
     DBuf<double> x, r, z, p, q, ud, fe, partials, cvec, xl64;
     DBuf<float> xl32;
@@ -261,285 +218,6 @@ void build_geometry(gl_ctx *c) {
 
 // ---------------------------------------------------------------- decomposition
 
-void build_boxes(gl_ctx *c) {
-    const MeshHost &m = c->m;
-    const gl_opts &o = c->opts;
-    auto rx = split_range(m.nx, o.px), ry = split_range(m.ny, o.py), rz = split_range(m.nz, o.pz);
-    const int ne[3] = {m.nx, m.ny, m.nz};
-    c->boxes.clear();
-    for (int kz = 0; kz < o.pz; ++kz)
-        for (int ky = 0; ky < o.py; ++ky)
-            for (int kx = 0; kx < o.px; ++kx) {
-                SubBox b{};
-                std::pair<int, int> core[3] = {rx[kx], ry[ky], rz[kz]};
-                for (int d = 0; d < 3; ++d) {
-                    int lo = std::max(0, core[d].first - o.overlap), hi = std::min(ne[d], core[d].second + o.overlap);
-                    b.ebox[2 * d] = lo;
-                    b.ebox[2 * d + 1] = hi;
-                    b.nbox[2 * d] = 2 * lo;
-                    b.nbox[2 * d + 1] = 2 * hi;
-                    b.art[2 * d] = lo > 0;
-                    b.art[2 * d + 1] = hi < ne[d];
-                }
-                c->boxes.push_back(b);
-            }
-}
-
-// Element -> local index maps of one plan's subdomains.
-void build_local_elems(const MeshHost &m, const std::vector<SubBox> &boxes, const FactorPlan &P, LocalElems &E,
-                       cudaStream_t s) {
-    std::vector<int> elem, sub, loc;
-    for (int j = 0; j < P.n_sub; ++j) {
-        const SubBox &b = boxes[j];
-        const int nbx = b.nbox[1] - b.nbox[0] + 1, nby = b.nbox[3] - b.nbox[2] + 1, nbz = b.nbox[5] - b.nbox[4] + 1;
-        std::vector<int> map((size_t)nbx * nby * nbz * 3, -1);
-        const int64_t off = P.vec_off[j];
-        for (int64_t i = 0; i < P.vec_len[j]; ++i) {
-            int64_t g = P.h_gdof[off + i];
-            int64_t node = g / 3;
-            int comp = (int)(g % 3);
-            int x = (int)(node % m.NX), y = (int)((node / m.NX) % m.NY), z = (int)(node / ((int64_t)m.NX * m.NY));
-            map[3 * ((size_t)(x - b.nbox[0]) + (size_t)nbx * ((y - b.nbox[2]) + (size_t)nby * (z - b.nbox[4]))) + comp] =
-                (int)i;
-        }
-        for (int ez = b.ebox[4]; ez < b.ebox[5]; ++ez)
-            for (int ey = b.ebox[2]; ey < b.ebox[3]; ++ey)
-                for (int ex = b.ebox[0]; ex < b.ebox[1]; ++ex) {
-                    elem.push_back((int)(ex + (int64_t)m.nx * (ey + (int64_t)m.ny * ez)));
-                    sub.push_back(j);
-                    for (int a = 0; a < 27; ++a) {
-                        int x = 2 * ex + a % 3 - b.nbox[0], y = 2 * ey + (a / 3) % 3 - b.nbox[2],
-                            z = 2 * ez + a / 9 - b.nbox[4];
-                        for (int cc = 0; cc < 3; ++cc)
-                            loc.push_back(map[3 * ((size_t)x + (size_t)nbx * (y + (size_t)nby * z)) + cc]);
-                    }
-                }
-    }
-    E.n_pairs = (int64_t)elem.size();
-    E.elem.upload(elem, s);
-    E.sub.upload(sub, s);
-    E.loc.upload(loc, s);
-    GL_CUDA(cudaStreamSynchronize(s));
-}
-
-// Copies the first m of k columns of a multi-vector (per-subdomain layout).
-__global__ void k_copy_cols(const int64_t *__restrict__ voff, const int64_t *__restrict__ vlen,
-                            const double *__restrict__ X, int k, double *__restrict__ Y, int mcols) {
-    const int s = blockIdx.x;
-    const int64_t n = vlen[s];
-    for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < n * mcols; i += (int64_t)gridDim.y * blockDim.x) {
-        int64_t a = i / n, r = i % n;
-        Y[voff[s] * mcols + a * n + r] = X[voff[s] * k + a * n + r];
-    }
-}
-
-// G (N x m, column stride N) [gdof_j[i], :] (+)= Y_j[i, :]
-__global__ void k_scatter_cols(const int64_t *__restrict__ gdof, int64_t off, int64_t n, const double *__restrict__ Y,
-                               int64_t yoff, int m, double *__restrict__ G, int64_t N, int zero) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * m; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t a = i / n, r = i % n;
-        G[a * N + gdof[off + r]] = zero ? 0.0 : Y[yoff + a * n + r];
-    }
-}
-
-// K0[(l*m + a) + (j*m + b) * n0] = sum_i Z_l[i, a] G[gdof_l[i], b]
-__global__ void __launch_bounds__(256) k_coarse_block(const int64_t *__restrict__ gdof, int64_t off, int64_t n,
-                                                      const double *__restrict__ Z, int64_t zoff, int m,
-                                                      const double *__restrict__ G, int64_t N, double *__restrict__ K0,
-                                                      int64_t n0, int row0, int col0) {
-    const int a = blockIdx.x / m, b = blockIdx.x % m;
-    double v = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += Z[zoff + a * n + i] * G[b * N + gdof[off + i]];
-    __shared__ double red[256];
-    red[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) K0[(row0 + a) + (int64_t)(col0 + b) * n0] = red[0];
-}
-
-void build_geneo(gl_ctx *c, const std::vector<uint8_t> &is_dir) {
-    const MeshHost &m = c->m;
-    cudaStream_t s = c->stream;
-    const int nev = c->opts.nev;
-    const double sigma = c->opts.sigma > 0 ? c->opts.sigma : 1e-3;
-    const int nsub = (int)c->boxes.size();
-    // Neumann symbolic: all free DOFs of each closed subdomain
-    std::vector<SubSymbolic> syms(nsub);
-    parallel_for(nsub, [&](int j) { build_symbolic(m, c->boxes[j], is_dir, true, LEAF_NODES, syms[j]); });
-    build_plan(syms, c->PN, s);
-    stamp(c, "Neumann symbolic");
-    FactorPlan &PN = c->PN;
-    for (int j = 0; j < nsub; ++j)
-        if (PN.vec_len[j] < nev) fail(GL_ERR_INVALID_ARG, "subdomain has fewer DOFs than nev");
-    // partition of unity: 1/multiplicity over the Dirichlet (interior) sets, 0 on artificial boundaries
-    std::vector<int> mult(m.n_dof, 0);
-    for (int64_t g : c->PD.h_gdof) mult[g] += 1;
-    std::vector<double> xi(PN.n_local, 0.0);
-    for (int j = 0; j < nsub; ++j) {
-        const SubBox &b = c->boxes[j];
-        for (int64_t i = 0; i < PN.vec_len[j]; ++i) {
-            int64_t g = PN.h_gdof[PN.vec_off[j] + i];
-            int64_t node = g / 3;
-            int pos[3] = {(int)(node % m.NX), (int)((node / m.NX) % m.NY), (int)(node / ((int64_t)m.NX * m.NY))};
-            bool art = false;
-            for (int d = 0; d < 3; ++d) {
-                if (b.art[2 * d] && pos[d] == b.nbox[2 * d]) art = true;
-                if (b.art[2 * d + 1] && pos[d] == b.nbox[2 * d + 1]) art = true;
-            }
-            if (!art) {
-                if (mult[g] == 0) fail(GL_ERR_INVALID_ARG, "a free DOF lies in no subdomain interior (overlap >= 1?)");
-                xi[PN.vec_off[j] + i] = 1.0 / mult[g];
-            }
-        }
-    }
-    DBuf<double> d_xi;
-    d_xi.upload(xi, s);
-    const int k = std::min(32, std::max(nev + 4, ((2 * nev + 3) / 4) * 4));
-    const int64_t nl = PN.n_local;
-    c->m_coarse = nev;
-    c->n0 = nsub * nev;
-    c->Z.alloc(nl * nev);
-    c->eig.assign((size_t)nsub * nev, 0.0);
-    const int iters = c->opts.eig_iters > 0 ? c->opts.eig_iters : 100;
-    // Groups of subdomains: factor of A^N + sigma Xi A^N Xi and block subspace
-    // iteration for the largest mu of B p = mu M p, one group at a time.
-    const int64_t budget = (int64_t)(40e9 / sizeof(double));   // factor entries per group
-    int j0 = 0, max_its = 0;
-    while (j0 < nsub) {
-        int j1 = j0;
-        int64_t acc = 0;
-        while (j1 < nsub && (j1 == j0 || acc + syms[j1].l_size <= budget)) acc += syms[j1++].l_size;
-        const int ng = j1 - j0;
-        std::vector<SubSymbolic> gs(syms.begin() + j0, syms.begin() + j1);
-        FactorPlan PG;
-        build_plan(gs, PG, s);
-        gs.clear();
-        const int64_t goff = PN.vec_off[j0], gl = PG.n_local;
-        DBuf<double> LN;
-        LN.alloc(PG.l_size);
-        const double *xg = d_xi.p + goff;
-        numeric_factor<double>(PG, c->d_C.p, c->d_geo.p, xg, sigma, LN.p, c->err.p, s);
-        check_err(c, "GenEO shifted Neumann factorisation");
-        stamp(c, "Neumann factorisation (group)");
-        std::vector<SubBox> gboxes(c->boxes.begin() + j0, c->boxes.begin() + j1);
-        LocalElems E;
-        build_local_elems(m, gboxes, PG, E, s);
-        DBuf<double> V, BV, BW, tmp, GB, GM, Y, mu;
-        V.alloc(gl * k);
-        BV.alloc(gl * k);
-        BW.alloc(gl * k);
-        tmp.alloc(gl * k);
-        GB.alloc((size_t)ng * k * k);
-        GM.alloc((size_t)ng * k * k);
-        Y.alloc((size_t)ng * k * k);
-        mu.alloc((size_t)ng * k);
-        fill_random(V.p, gl * k, 0x1707042280000001ull + (uint64_t)j0, s);
-        BV.zero(s);
-        local_K_apply(PG, E, c->d_C.p, c->d_geo.p, xg, V.p, BV.p, k, s);          // BV = Xi A^N Xi V
-        std::vector<double> mu_prev((size_t)ng * k, 0.0), mu_now((size_t)ng * k);
-        int it = 0;
-        for (; it < iters; ++it) {
-            // W = M^{-1} B V
-            GL_CUDA(cudaMemcpyAsync(tmp.p, BV.p, sizeof(double) * gl * k, cudaMemcpyDeviceToDevice, s));
-            factor_solve<double>(PG, LN.p, tmp.p, k, s);
-            std::swap(V.p, tmp.p);
-            BW.zero(s);
-            local_K_apply(PG, E, c->d_C.p, c->d_geo.p, xg, V.p, BW.p, k, s);       // BW = B W
-            local_gram(PG, V.p, BV.p, k, GM.p, s);                  // W^T M W = W^T (B V)
-            local_gram(PG, V.p, BW.p, k, GB.p, s);                  // W^T B W
-            small_geneig(ng, k, GB.p, GM.p, Y.p, mu.p, c->err.p, s);
-            check_err(c, "GenEO Rayleigh-Ritz");
-            local_rotate(PG, V.p, Y.p, k, tmp.p, s);
-            local_rotate(PG, BW.p, Y.p, k, tmp.p, s);
-            std::swap(BV.p, BW.p);
-            GL_CUDA(cudaMemcpyAsync(mu_now.data(), mu.p, mu_now.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-            GL_CUDA(cudaStreamSynchronize(s));
-            double change = 0.0;
-            for (int j = 0; j < ng; ++j)
-                for (int a = 0; a < nev; ++a) {
-                    double now = mu_now[(size_t)j * k + a], prev = mu_prev[(size_t)j * k + a];
-                    change = std::max(change, std::fabs(now - prev) / std::fabs(now));
-                }
-            mu_prev = mu_now;
-            // Ritz values settle to ~(rate)^{2 it}; 1e-12 leaves the Ritz vectors accurate to
-            // about 1e-6, far below what changes the coarse space's effect on PCG.
-            if (it >= 4 && change < 1e-12) {
-                ++it;
-                break;
-            }
-        }
-        if (std::getenv("GL_VERBOSE")) {
-            double worst = 0.0, lo = 1e300, hi = 0.0;
-            for (int j = 0; j < ng; ++j) {
-                double lm = 1.0 / mu_now[(size_t)j * k + nev - 1] - sigma, lk = 1.0 / mu_now[(size_t)j * k + k - 1] - sigma;
-                worst = std::max(worst, (lm + sigma) / (lk + sigma));
-                lo = std::min(lo, lm);
-                hi = std::max(hi, lm);
-            }
-            std::fprintf(stderr, "[gl]   group %d-%d: %d iterations, lambda_nev in [%.3g, %.3g], worst rate %.3f\n", j0,
-                         j1 - 1, it, lo, hi, worst);
-        }
-        max_its = std::max(max_its, it);
-        for (int j = 0; j < ng; ++j)
-            for (int a = 0; a < nev; ++a) c->eig[(size_t)(j0 + j) * nev + a] = 1.0 / mu_now[(size_t)j * k + a] - sigma;
-        // Z columns of these subdomains (global Neumann layout, nev columns)
-        for (int j = 0; j < ng; ++j) {
-            const int64_t n = PG.vec_len[j];
-            GL_CUDA(cudaMemcpy2DAsync(c->Z.p + PN.vec_off[j0 + j] * nev, n * sizeof(double), V.p + PG.vec_off[j] * k,
-                                      n * sizeof(double), n * sizeof(double), nev, cudaMemcpyDeviceToDevice, s));
-        }
-        stamp(c, "GenEO subspace iteration (group)");
-        j0 = j1;
-    }
-    c->eig_iters_done = max_its;
-    if (std::getenv("GL_VERBOSE")) std::fprintf(stderr, "[gl] GenEO subspace iterations (max over groups): %d\n", max_its);
-    syms.clear();
-    scale_rows(PN, c->Z.p, d_xi.p, nev, s);                        // Z = Xi p
-    LocalElems E;
-    build_local_elems(m, c->boxes, PN, E, s);
-    // K_0 = Z^T K Z: Y_j = A^N_j Z_j, then blocks against overlapping subdomains
-    DBuf<double> KZ, G;
-    KZ.alloc(nl * nev);
-    KZ.zero(s);
-    local_K_apply(PN, E, c->d_C.p, c->d_geo.p, nullptr, c->Z.p, KZ.p, nev, s);
-    G.alloc((size_t)m.n_dof * nev);
-    G.zero(s);
-    const int n0 = c->n0;
-    c->L0.alloc((size_t)n0 * n0);
-    c->L0.zero(s);
-    for (int j = 0; j < nsub; ++j) {
-        int64_t nj = PN.vec_len[j], oj = PN.vec_off[j];
-        k_scatter_cols<<<256, 256, 0, s>>>(PN.d_gdof.p, oj, nj, KZ.p, oj * nev, nev, G.p, m.n_dof, 0);
-        for (int l = 0; l < nsub; ++l) {
-            bool overlap = true;
-            for (int d = 0; d < 3; ++d)
-                if (c->boxes[l].nbox[2 * d] > c->boxes[j].nbox[2 * d + 1] ||
-                    c->boxes[j].nbox[2 * d] > c->boxes[l].nbox[2 * d + 1])
-                    overlap = false;
-            if (!overlap) continue;
-            k_coarse_block<<<nev * nev, 256, 0, s>>>(PN.d_gdof.p, PN.vec_off[l], PN.vec_len[l], c->Z.p,
-                                                     PN.vec_off[l] * nev, nev, G.p, m.n_dof, c->L0.p, n0, l * nev,
-                                                     j * nev);
-        }
-        k_scatter_cols<<<256, 256, 0, s>>>(PN.d_gdof.p, oj, nj, KZ.p, oj * nev, nev, G.p, m.n_dof, 1);
-        GL_CUDA(cudaGetLastError());
-    }
-    {
-        DBuf<double> K0inv;
-        K0inv.alloc((size_t)n0 * n0);
-        dense_inverse(c->L0.p, n0, K0inv.p, c->err.p, s);
-        c->L0 = std::move(K0inv);
-    }
-    check_err(c, "coarse Cholesky");
-    GL_CUDA(cudaStreamSynchronize(s));
-}
-
-// ---------------------------------------------------------------- operator pieces
-
-// Per-phase CUDA-event timing (only when profiling is on).  Each phase keeps
 // one start/stop pair; a pending pair is folded into the totals before reuse.
 void prof_fold(gl_ctx *c, int ph) {
     Prof &P = c->prof;
@@ -592,11 +270,9 @@ void apply_prec(gl_ctx *c, const double *r, double *z) {
     }
     prof_end(c, PH_LOCAL);
     g_launches += 2 + factor_solve_launches(c->PD);
-    if (c->n0 > 0) {
+    if (c->co.n0 > 0) {
         prof_begin(c, PH_COARSE);
-        coarse_restrict(c->PN, c->Z.p, c->m_coarse, r, c->cvec.p, s);
-        dense_symv(c->L0.p, c->n0, c->cvec.p, c->cvec2.p, s);
-        coarse_prolong(c->PN, c->Z.p, c->m_coarse, c->cvec2.p, z, s);
+        coarse_apply(c->co, r, z, c->cvec.p, c->cvec2.p, s);
         prof_end(c, PH_COARSE);
         g_launches += 3;
     }
@@ -627,12 +303,31 @@ void setup(gl_ctx *c, const gl_opts &o) {
     std::vector<uint8_t> is_dir(m.n_dof, 0);
     for (int64_t d : c->dir_dof) is_dir[d] = 1;
     c->n_free = m.n_dof - (int64_t)std::count(is_dir.begin(), is_dir.end(), (uint8_t)1);
-    build_boxes(c);
-    const int nsub = (int)c->boxes.size();
-    std::vector<SubSymbolic> syms(nsub);
-    parallel_for(nsub, [&](int j) { build_symbolic(m, c->boxes[j], is_dir, false, LEAF_NODES, syms[j]); });
-    build_plan(syms, c->PD, s);
-    syms.clear();
+    // the laminate as a one-part problem
+    Problem &P = c->prob;
+    P = Problem();
+    P.stream = s;
+    P.d_err = c->err.p;
+    P.n_dof = m.n_dof;
+    P.n_elem = m.n_elem;
+    P.C = c->d_C.p;
+    P.geo = c->d_geo.p;
+    P.stamp = [c](const char *w) { stamp(c, w); };
+    part_boxes(m, c->opts.px, c->opts.py, c->opts.pz, c->opts.overlap, P.boxes);
+    {
+        Part pt;
+        pt.m = &c->m;
+        pt.is_dir = is_dir;
+        pt.sub0 = 0;
+        pt.sub1 = (int)P.boxes.size();
+        P.parts.push_back(std::move(pt));
+    }
+    P.sub_part.assign(P.boxes.size(), 0);
+    {
+        std::vector<SubSymbolic> syms;
+        problem_symbolic(P, false, LEAF_NODES, syms);
+        build_plan(syms, c->PD, s);
+    }
     stamp(c, "Dirichlet symbolic");
     if (c->opts.precision == GL_PREC_MIXED) {
         c->LD64.release();
@@ -645,17 +340,17 @@ void setup(gl_ctx *c, const gl_opts &o) {
     }
     check_err(c, "local Dirichlet factorisation");
     stamp(c, "Dirichlet factorisation");
-    c->n0 = 0;
-    c->m_coarse = 0;
-    c->eig.clear();
-    if (c->opts.nev > 0) build_geneo(c, is_dir);
+    c->co = Coarse();
+    if (c->opts.nev > 0) problem_coarse(P, c->opts, c->PD, LEAF_NODES, c->co);
+    if (std::getenv("GL_VERBOSE"))
+        std::fprintf(stderr, "[gl] GenEO subspace iterations (max over groups): %d\n", c->co.eig_iters);
     stamp(c, "GenEO coarse space + K0");
     // work vectors
     const int64_t N = m.n_dof;
     for (DBuf<double> *b : {&c->x, &c->r, &c->z, &c->p, &c->q, &c->ud, &c->fe}) b->alloc(N);
     c->partials.alloc(1024);
-    c->cvec.alloc(std::max(1, c->n0));
-    c->cvec2.alloc(std::max(1, c->n0));
+    c->cvec.alloc(std::max(1, c->co.n0));
+    c->cvec2.alloc(std::max(1, c->co.n0));
     if (c->opts.precision == GL_PREC_MIXED) {
         c->xl32.alloc(c->PD.n_local);
         c->xl64.release();
@@ -782,12 +477,410 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info, bool homogeneou
         info->ms_setup = c->ms_setup;
         info->ms_solve = ms;
         info->n_free = c->n_free;
-        info->n_coarse = c->n0;
+        info->n_coarse = c->co.n0;
         info->factor_nnz = c->PD.l_size;
     }
     if (status != GL_OK) {
         g_last_error = status == GL_ERR_NAN ? "NaN/Inf in the PCG iteration" : "PCG reached max_iter";
         throw Error{status, g_last_error};
+    }
+}
+
+}  // namespace
+
+// ====================================================================== many laminates at once
+
+struct gl_batch {
+    int device = 0;
+    cudaStream_t stream = 0;
+    bool own_stream = false, ready = false;
+    std::vector<gl_ctx *> items;
+    gl_opts opts{};
+    Problem prob;
+    FactorPlan PD;
+    DBuf<double> LD64;
+    DBuf<float> LD32;
+    Coarse co;
+    std::vector<PartDesc> parts;
+    DBuf<PartDesc> d_parts;
+    std::vector<std::array<int, 2>> grid;     // (px, py) per laminate
+    std::vector<int64_t> n_free;
+    int64_t N = 0, E = 0, ndir = 0;
+    DBuf<double> C, geo, f, x, r, z, p, q, ud, fe, c1, c2, xl64, partials, scal;
+    DBuf<float> xl32;
+    DBuf<int> ints;                           // active (n), iters (n), n_active (1)
+    DBuf<int64_t> d_dir;
+    DBuf<double> d_dirval;
+    DBuf<int> err;
+    int *h_active = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double ms_setup = 0;
+    ~gl_batch() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        if (h_active) cudaFreeHost(h_active);
+        if (own_stream) cudaStreamDestroy(stream);
+    }
+    SegScalars seg() {
+        const int n = (int)items.size();
+        return SegScalars{scal.p, scal.p + n, scal.p + 2 * n, scal.p + 3 * n, scal.p + 4 * n, scal.p + 5 * n,
+                          ints.p, ints.p + n};
+    }
+};
+
+namespace {
+
+// Decomposition autotuner: candidates are in-plane grids (px, py, 1) with
+// 8 <= px py <= 64 whose element boxes have an aspect ratio within [1/2, 2]
+// (all of them if none qualifies).  For each, the symbolic factorisation of
+// the central subdomain gives factor entries and factorisation flops, scaled
+// by the subdomain count; the predicted time of one solve is
+//   setup = (Dirichlet flops + 2x for the Neumann factor) / F
+//         + 25 subspace iterations x 2 nev vectors x 4 flops x 1.6 nnz / F
+//         + (2 n0)^3 / 3 / F                     (coarse inverse)
+//   iteration = max(16 nnz / B, 4 nnz / F)       (FP64 sweeps; 8 nnz / B mixed)
+//   total = setup + 40 iterations,
+// with F = 0.8e12 flop/s (FP64) and B = 4.5e12 B/s (sustained HBM); the ratios
+// Neumann/Dirichlet (1.6x entries, 2x flops) were measured on the corner laminate.
+std::array<int, 2> autotune_grid(const MeshHost &m, const std::vector<uint8_t> &is_dir, int overlap, int nev,
+                                 bool mixed) {
+    const double F = 0.8e12, B = 4.5e12;
+    struct Cand {
+        int px, py;
+    };
+    std::vector<Cand> cands, all;
+    for (int px = 1; px <= std::min(64, m.nx); ++px)
+        for (int py = 1; py <= std::min(64, m.ny); ++py) {
+            const int ns = px * py;
+            if (ns < 8 || ns > 64) continue;
+            all.push_back({px, py});
+            const double ax = (double)m.nx / px, ay = (double)m.ny / py;
+            if (ax <= 2 * ay && ay <= 2 * ax) cands.push_back({px, py});
+        }
+    if (cands.empty()) cands = all;
+    if (cands.empty()) return {std::min(m.nx, 2), std::min(m.ny, 2)};
+    double best = 1e300;
+    std::array<int, 2> pick = {cands[0].px, cands[0].py};
+    for (const Cand &cd : cands) {
+        std::vector<SubBox> boxes;
+        part_boxes(m, cd.px, cd.py, 1, overlap, boxes);
+        SubSymbolic S;
+        build_symbolic(m, boxes[(cd.py / 2) * cd.px + cd.px / 2], is_dir, false, LEAF_NODES, S);
+        const int ns = cd.px * cd.py;
+        double fl = 0.0;
+        for (const Supernode &sn : S.sn) {
+            const double f = sn.p + sn.q;
+            for (int j = 0; j < sn.p; ++j) fl += (f - j) * (f - j);
+        }
+        const double nnz = (double)S.l_size * ns, flops = fl * ns, n0 = (double)ns * nev;
+        const double setup = (mixed ? 0.1 : 1.0) * flops / F + 2.0 * flops / F + 25.0 * 2 * nev * 4.0 * 1.6 * nnz / F +
+                             8.0 * n0 * n0 * n0 / 3.0 / F;
+        const double iter = mixed ? 8.0 * nnz / B : std::max(16.0 * nnz / B, 4.0 * nnz / F);
+        const double cost = setup + 40.0 * iter;
+        if (cost < best) {
+            best = cost;
+            pick = {cd.px, cd.py};
+        }
+    }
+    return pick;
+}
+
+__global__ void k_seg_init(SegScalars S, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    S.iters[i] = 0;
+    S.active[i] = S.ff[i] > 0.0 ? 1 : 0;
+    S.rz_old[i] = 0.0;
+}
+
+void batch_precond(gl_batch *b, const double *r, double *z) {
+    cudaStream_t s = b->stream;
+    GL_CUDA(cudaMemsetAsync(z, 0, b->N * sizeof(double), s));
+    if (b->opts.precision == GL_PREC_MIXED) {
+        gather_local<float>(b->PD, r, b->xl32.p, s);
+        factor_solve<float>(b->PD, b->LD32.p, b->xl32.p, 1, s);
+        scatter_add_local<float>(b->PD, b->xl32.p, z, s);
+    } else {
+        gather_local<double>(b->PD, r, b->xl64.p, s);
+        factor_solve<double>(b->PD, b->LD64.p, b->xl64.p, 1, s);
+        scatter_add_local<double>(b->PD, b->xl64.p, z, s);
+    }
+    g_launches += 2 + factor_solve_launches(b->PD);
+    if (b->co.n0 > 0) {
+        coarse_apply(b->co, r, z, b->c1.p, b->c2.p, s);
+        g_launches += 3;
+    }
+}
+
+void batch_ku(gl_batch *b, const double *x, double *y) {
+    launch_ku_batch(b->d_parts.p, (int)b->parts.size(), b->E, b->N, b->C.p, b->geo.p, x, y, b->stream);
+    g_launches += 1;
+}
+
+void batch_setup(gl_batch *b, const gl_opts &o) {
+    auto t0 = std::chrono::steady_clock::now();
+    GL_REQUIRE(o.overlap >= 1, "overlap must be >= 1");
+    GL_REQUIRE(o.nev >= 0 && o.nev <= 28, "nev must be in [0, 28]");
+    GL_REQUIRE(o.precision == GL_PREC_FP64 || o.precision == GL_PREC_MIXED, "unknown precision mode");
+    b->ready = false;
+    b->opts = o;
+    if (b->opts.max_iter <= 0) b->opts.max_iter = 2000;
+    if (b->opts.tol <= 0) b->opts.tol = 1e-10;
+    if (b->opts.resid_period <= 0) b->opts.resid_period = 50;
+    cudaStream_t s = b->stream;
+    const int n = (int)b->items.size();
+    if (!b->err.p) {
+        b->err.alloc(1);
+        b->err.zero(s);
+    }
+    // geometry and loads of every laminate, on the batch stream
+    b->parts.clear();
+    b->N = b->E = 0;
+    std::vector<std::vector<uint8_t>> is_dir(n);
+    b->n_free.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        gl_ctx *c = b->items[i];
+        if (!c->have_mat || !c->have_mesh) fail(GL_ERR_STATE, "batch: every laminate needs materials and a mesh");
+        c->stream = s;
+        build_geometry(c);
+        const MeshHost &m = c->m;
+        PartDesc pd{};
+        pd.elem_off = b->E;
+        pd.dof_off = b->N;
+        pd.n_dof = m.n_dof;
+        pd.nx = m.nx;
+        pd.ny = m.ny;
+        pd.NX = m.NX;
+        pd.NY = m.NY;
+        b->parts.push_back(pd);
+        b->N += m.n_dof;
+        b->E += m.n_elem;
+        is_dir[i].assign(m.n_dof, 0);
+        for (int64_t d : c->dir_dof) is_dir[i][d] = 1;
+        b->n_free[i] = m.n_dof - (int64_t)c->dir_dof.size();
+    }
+    GL_REQUIRE(b->E < ((int64_t)1 << 31), "batch too large for 32-bit element ids");
+    b->d_parts.upload(b->parts, s);
+    b->C.alloc(36 * b->E);
+    b->geo.alloc(270 * b->E);
+    b->f.alloc(b->N);
+    std::vector<int64_t> hdir;
+    std::vector<double> hval;
+    for (int i = 0; i < n; ++i) {
+        gl_ctx *c = b->items[i];
+        const PartDesc &pd = b->parts[i];
+        GL_CUDA(cudaMemcpyAsync(b->C.p + 36 * pd.elem_off, c->d_C.p, 36 * c->m.n_elem * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+        GL_CUDA(cudaMemcpyAsync(b->geo.p + 270 * pd.elem_off, c->d_geo.p, 270 * c->m.n_elem * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+        GL_CUDA(cudaMemcpyAsync(b->f.p + pd.dof_off, c->d_ftrac.p, c->m.n_dof * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+        for (size_t k = 0; k < c->dir_dof.size(); ++k) {
+            hdir.push_back(c->dir_dof[k] + pd.dof_off);
+            hval.push_back(c->dir_val[k]);
+        }
+    }
+    b->ndir = (int64_t)hdir.size();
+    b->d_dir.upload(hdir, s);
+    b->d_dirval.upload(hval, s);
+    // decomposition: given grid, or the autotuner per laminate
+    b->grid.assign(n, {o.px, o.py});
+    if (o.px <= 0 || o.py <= 0) {
+        std::vector<std::thread> th;
+        std::atomic<int> next(0);
+        const int nt = std::max(1, std::min(n, (int)std::thread::hardware_concurrency()));
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&]() {
+                for (int i = next++; i < n; i = next++)
+                    b->grid[i] = autotune_grid(b->items[i]->m, is_dir[i], o.overlap, o.nev,
+                                               o.precision == GL_PREC_MIXED);
+            });
+        for (auto &t : th) t.join();
+    }
+    Problem &P = b->prob;
+    P = Problem();
+    P.stream = s;
+    P.d_err = b->err.p;
+    P.n_dof = b->N;
+    P.n_elem = b->E;
+    P.C = b->C.p;
+    P.geo = b->geo.p;
+    for (int i = 0; i < n; ++i) {
+        const MeshHost &m = b->items[i]->m;
+        const int px = std::min(b->grid[i][0], m.nx), py = std::min(b->grid[i][1], m.ny);
+        b->grid[i] = {px, py};
+        Part pt;
+        pt.m = &m;
+        pt.is_dir = std::move(is_dir[i]);
+        pt.dof_off = b->parts[i].dof_off;
+        pt.elem_off = b->parts[i].elem_off;
+        pt.sub0 = (int)P.boxes.size();
+        part_boxes(m, px, py, 1, o.overlap, P.boxes);
+        pt.sub1 = (int)P.boxes.size();
+        P.sub_part.resize(P.boxes.size(), i);
+        P.parts.push_back(std::move(pt));
+    }
+    {
+        std::vector<SubSymbolic> syms;
+        problem_symbolic(P, false, LEAF_NODES, syms);
+        build_plan(syms, b->PD, s);
+    }
+    if (b->opts.precision == GL_PREC_MIXED) {
+        b->LD64.release();
+        b->LD32.alloc(b->PD.l_size);
+        numeric_factor<float>(b->PD, b->C.p, b->geo.p, nullptr, 0.0, b->LD32.p, b->err.p, s);
+    } else {
+        b->LD32.release();
+        b->LD64.alloc(b->PD.l_size);
+        numeric_factor<double>(b->PD, b->C.p, b->geo.p, nullptr, 0.0, b->LD64.p, b->err.p, s);
+    }
+    {
+        int h = 0;
+        GL_CUDA(cudaMemcpyAsync(&h, b->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        if (h) {
+            b->err.zero(s);
+            fail(GL_ERR_NOT_SPD, "batch local Dirichlet factorisation: non-positive pivot");
+        }
+    }
+    b->co = Coarse();
+    if (b->opts.nev > 0) problem_coarse(P, b->opts, b->PD, LEAF_NODES, b->co);
+    for (DBuf<double> *v : {&b->x, &b->r, &b->z, &b->p, &b->q, &b->ud, &b->fe}) v->alloc(b->N);
+    b->c1.alloc(std::max(1, b->co.n0));
+    b->c2.alloc(std::max(1, b->co.n0));
+    if (b->opts.precision == GL_PREC_MIXED) b->xl32.alloc(b->PD.n_local);
+    else b->xl64.alloc(b->PD.n_local);
+    b->partials.alloc((size_t)n * SEG_BLOCKS);
+    b->scal.alloc((size_t)6 * n);
+    b->scal.zero(s);
+    b->ints.alloc((size_t)2 * n + 1);
+    b->ints.zero(s);
+    if (!b->h_active) GL_CUDA(cudaMallocHost(&b->h_active, sizeof(int)));
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    GL_CUDA(cudaStreamSynchronize(s));
+    b->ready = true;
+    b->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// One PCG iteration of every active laminate (captured once into a CUDA graph).
+void batch_iteration(gl_batch *b) {
+    cudaStream_t s = b->stream;
+    const int n = (int)b->items.size();
+    const int64_t N = b->N;
+    SegScalars S = b->seg();
+    batch_ku(b, b->p.p, b->q.p);
+    set_entries(b->q.p, b->d_dir.p, b->ndir, nullptr, s);
+    seg_dot(b->p.p, b->q.p, b->d_parts.p, n, b->partials.p, S.pq, s);
+    seg_update_xr(b->x.p, b->r.p, b->p.p, b->q.p, b->d_parts.p, n, S, b->partials.p, s);
+    seg_check(S, n, b->opts.tol, b->opts.max_iter, b->ints.p + 2 * n, s);
+    if (b->opts.precision == GL_PREC_MIXED) seg_dot(b->r.p, b->z.p, b->d_parts.p, n, b->partials.p, S.rz_old, s);
+    batch_precond(b, b->r.p, b->z.p);
+    seg_dot(b->r.p, b->z.p, b->d_parts.p, n, b->partials.p, S.rho_new, s);
+    seg_update_p(b->p.p, b->z.p, b->d_parts.p, n, S, s);
+    (void)N;
+}
+
+void batch_solve(gl_batch *b, double *const *u, gl_info *infos) {
+    if (!b->ready) fail(GL_ERR_STATE, "gl_batch_solve before gl_batch_setup");
+    cudaStream_t s = b->stream;
+    const int n = (int)b->items.size();
+    const int64_t N = b->N;
+    SegScalars S = b->seg();
+    cudaEvent_t e0, e1;
+    GL_CUDA(cudaEventCreate(&e0));
+    GL_CUDA(cudaEventCreate(&e1));
+    GL_CUDA(cudaEventRecord(e0, s));
+    // fe = f - K u_D on the free DOFs
+    b->ud.zero(s);
+    set_entries(b->ud.p, b->d_dir.p, b->ndir, b->d_dirval.p, s);
+    batch_ku(b, b->ud.p, b->q.p);
+    sub(b->fe.p, b->f.p, b->q.p, N, s);
+    set_entries(b->fe.p, b->d_dir.p, b->ndir, nullptr, s);
+    seg_dot(b->fe.p, b->fe.p, b->d_parts.p, n, b->partials.p, S.ff, s);
+    k_seg_init<<<(n + 127) / 128, 128, 0, s>>>(S, n);
+    b->x.zero(s);
+    GL_CUDA(cudaMemcpyAsync(b->r.p, b->fe.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    batch_precond(b, b->r.p, b->z.p);
+    seg_dot(b->r.p, b->z.p, b->d_parts.p, n, b->partials.p, S.rho, s);
+    GL_CUDA(cudaMemcpyAsync(b->p.p, b->z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    g_launches += 2 * (b->ndir ? 1 : 0) + 6;
+    if (!b->gexec) {
+        GL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const long long before = g_launches.load();
+        batch_iteration(b);
+        g_launches.store(before);   // counted per replay below
+        GL_CUDA(cudaStreamEndCapture(s, &b->graph));
+        GL_CUDA(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+    }
+    const int per_iter = 6 + (b->ndir ? 1 : 0) + (b->opts.precision == GL_PREC_MIXED ? 2 : 0) + 2 +
+                         (int)factor_solve_launches(b->PD) + (b->co.n0 > 0 ? 3 : 0) + 4;
+    const int period = b->opts.resid_period;
+    for (int it = 1; it <= b->opts.max_iter; ++it) {
+        GL_CUDA(cudaGraphLaunch(b->gexec, s));
+        g_launches += per_iter;
+        GL_CUDA(cudaMemcpyAsync(b->h_active, b->ints.p + 2 * n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        if (*b->h_active == 0) break;
+        if (b->opts.precision == GL_PREC_MIXED && it % period == 0) {
+            // FP64 residual replacement r = fe - K x (frozen laminates keep their r: x is unchanged)
+            batch_ku(b, b->x.p, b->q.p);
+            set_entries(b->q.p, b->d_dir.p, b->ndir, nullptr, s);
+            sub(b->r.p, b->fe.p, b->q.p, N, s);
+            g_launches += 2 + (b->ndir ? 1 : 0);
+        }
+    }
+    // results: recurrence residuals, FP64 true residuals, displacements
+    std::vector<double> hs((size_t)6 * n);
+    std::vector<int> hi((size_t)2 * n);
+    GL_CUDA(cudaMemcpyAsync(hs.data(), b->scal.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaMemcpyAsync(hi.data(), b->ints.p, hi.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    batch_ku(b, b->x.p, b->q.p);
+    set_entries(b->q.p, b->d_dir.p, b->ndir, nullptr, s);
+    sub(b->r.p, b->fe.p, b->q.p, N, s);
+    seg_dot(b->r.p, b->r.p, b->d_parts.p, n, b->partials.p, S.rr, s);
+    axpy(b->x.p, 1.0, b->ud.p, N, s);
+    g_launches += 6;
+    std::vector<double> hrt(n);
+    GL_CUDA(cudaMemcpyAsync(hrt.data(), S.rr, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GL_CUDA(cudaEventRecord(e1, s));
+    GL_CUDA(cudaStreamSynchronize(s));
+    float ms = 0;
+    GL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int worst = GL_OK;
+    for (int i = 0; i < n; ++i) {
+        const double ff = hs[4 * n + i], rr = hs[3 * n + i];
+        const int iters = hi[n + i];
+        int st = GL_OK;
+        if (!std::isfinite(rr)) st = GL_ERR_NAN;
+        else if (ff > 0 && rr > b->opts.tol * b->opts.tol * ff) st = GL_ERR_NOT_CONVERGED;
+        if (st != GL_OK) worst = st;
+        if (u[i]) from_device(u[i], b->x.p + b->parts[i].dof_off, b->parts[i].n_dof, s);
+        if (infos) {
+            gl_info &in = infos[i];
+            in.iters = iters;
+            in.status = st;
+            in.rel_resid = ff > 0 ? std::sqrt(rr / ff) : 0.0;
+            in.rel_resid_true = ff > 0 ? std::sqrt(hrt[i] / ff) : 0.0;
+            in.ms_setup = b->ms_setup;
+            in.ms_solve = ms;
+            in.n_free = b->n_free[i];
+            in.n_coarse = (int)(b->co.n0 ? b->co.kn[i] : 0);
+            in.factor_nnz = b->PD.l_size;
+        }
+    }
+    if (worst != GL_OK) {
+        g_last_error = worst == GL_ERR_NAN ? "NaN/Inf in a batched PCG iteration" : "a laminate reached max_iter";
+        throw Error{worst, g_last_error};
     }
 }
 
@@ -1169,8 +1262,8 @@ int gl_profile_read(gl_ctx *c, gl_profile_data *out) {
         out->factor_bytes_per_entry = c->opts.precision == GL_PREC_MIXED ? 4 : 8;
         out->n_elem = c->m.n_elem;
         out->n_dof = c->m.n_dof;
-        out->n_sub = (int)c->boxes.size();
-        out->n_coarse_dim = c->n0;
+        out->n_sub = (int)c->prob.boxes.size();
+        out->n_coarse_dim = c->co.n0;
         out->factor_levels = 0;
         for (auto &L : c->PD.levels)
             if (!L.fronts.empty()) ++out->factor_levels;
@@ -1184,12 +1277,72 @@ int gl_geneo_eigenvalues(gl_ctx *c, double *lambda, int capacity, int *count) {
         require_ctx(c);
         if (!c->ready) fail(GL_ERR_STATE, "before gl_setup");
         GL_REQUIRE(count, "null count");
-        *count = (int)c->eig.size();
+        *count = (int)c->co.eig.size();
         if (lambda) {
-            GL_REQUIRE(capacity >= (int)c->eig.size(), "capacity too small");
-            std::copy(c->eig.begin(), c->eig.end(), lambda);
+            GL_REQUIRE(capacity >= (int)c->co.eig.size(), "capacity too small");
+            std::copy(c->co.eig.begin(), c->co.eig.end(), lambda);
         }
     });
+}
+
+int gl_batch_create(gl_batch **out, int n, gl_ctx *const *items, void *cuda_stream) {
+    return guard([&] {
+        GL_REQUIRE(out && n >= 1 && items, "need at least one laminate");
+        gl_batch *b = new gl_batch();
+        try {
+            b->device = items[0]->device;
+            for (int i = 0; i < n; ++i) {
+                GL_REQUIRE(items[i], "null laminate");
+                GL_REQUIRE(items[i]->device == b->device, "all laminates of a batch must be on one device");
+                for (int j = 0; j < i; ++j) GL_REQUIRE(items[j] != items[i], "a laminate appears twice in the batch");
+                b->items.push_back(items[i]);
+            }
+            GL_CUDA(cudaSetDevice(b->device));
+            if (cuda_stream) {
+                b->stream = (cudaStream_t)cuda_stream;
+            } else {
+                GL_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+                b->own_stream = true;
+            }
+        } catch (...) {
+            delete b;
+            throw;
+        }
+        *out = b;
+    });
+}
+
+int gl_batch_setup(gl_batch *b, const gl_opts *opts) {
+    return guard([&] {
+        GL_REQUIRE(b && opts, "null argument");
+        GL_CUDA(cudaSetDevice(b->device));
+        batch_setup(b, *opts);
+    });
+}
+
+int gl_batch_solve(gl_batch *b, double *const *u, gl_info *infos) {
+    return guard([&] {
+        GL_REQUIRE(b && u, "null argument");
+        GL_CUDA(cudaSetDevice(b->device));
+        batch_solve(b, u, infos);
+    });
+}
+
+int gl_batch_grid(const gl_batch *b, int *pxpy) {
+    return guard([&] {
+        GL_REQUIRE(b && pxpy && b->ready, "batch not set up");
+        for (size_t i = 0; i < b->grid.size(); ++i) {
+            pxpy[2 * i] = b->grid[i][0];
+            pxpy[2 * i + 1] = b->grid[i][1];
+        }
+    });
+}
+
+void gl_batch_destroy(gl_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    delete b;
 }
 
 }  // extern "C"

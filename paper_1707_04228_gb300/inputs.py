@@ -295,3 +295,34 @@ def flat_random(rng: np.random.Generator, n_inplane, n_plies, amp_deg, nsub=(2, 
 def random_vector(n, seed):
     """Seeded standard-normal FP64 vector."""
     return np.random.default_rng(seed).standard_normal(n)
+
+
+def batch_plates(count=96, seed=1707, dof_lo=40_000, dof_hi=800_000, nev=8):
+    """Flat laminates of uneven sizes and stackings for the batched solve.
+
+    Per laminate: a target size N ~ U[dof_lo, dof_hi]; a ply count P ~ U{4..24}
+    with 0.25 mm plies and 0.02 mm resin between them, one element per layer
+    (2P - 1 element layers); a square in-plane grid n x n, n in [10, 40],
+    chosen so that 3 (2n+1)^2 (2(2P-1)+1) is nearest the target (P is redrawn
+    until some n lands within 10%); ply angles iid from {0, +-45, 90}; a
+    Gaussian misalignment patch of amplitude U[0, 12] degrees; clamped at x = 0
+    with a 1 MPa x-traction at x = 20 mm.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        target = rng.uniform(dof_lo, dof_hi)
+        pick = None
+        for _ in range(200):
+            P = int(rng.integers(4, 25))
+            nz = 2 * P - 1
+            n = int(round((math.sqrt(target / (3.0 * (2 * nz + 1))) - 1.0) / 2.0))
+            if 10 <= n <= 40 and abs(3 * (2 * n + 1) ** 2 * (2 * nz + 1) - target) <= 0.1 * target:
+                pick = (n, P)
+                break
+        if pick is None:
+            continue
+        amp = float(rng.uniform(0.0, 12.0))
+        lam = flat_random(rng, pick[0], pick[1], amp, nsub=(0, 0, 1), nev=nev, name=f"plate_{len(out)}")
+        out.append(lam)
+    return out

@@ -87,6 +87,11 @@ SIGNATURES = {
     "gl_set_theta": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gl_stress_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(gl_info)]),
+    "gl_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p]),
+    "gl_batch_setup": (C.c_int, [C.c_void_p, C.POINTER(gl_opts)]),
+    "gl_batch_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gl_batch_grid": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gl_batch_destroy": (None, [C.c_void_p]),
     "gl_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "gl_profile_read": (C.c_int, [C.c_void_p, C.POINTER(gl_profile_data)]),
     "gl_kernel_launches": (C.c_longlong, []),
@@ -293,3 +298,61 @@ class Solver:
         if n.value:
             _check(self.lib, self.lib.gl_geneo_eigenvalues(self.ctx, _ptr(out), n.value, C.byref(n)))
         return out
+
+
+class Batch:
+    """Many laminates solved together (gl_batch_*): one launch per phase for all of them,
+    one PCG iteration replayed as a CUDA graph."""
+
+    def __init__(self, laminates, device=0, stream=None):
+        self.lib = load()
+        self.solvers = []
+        for lam in laminates:
+            s = Solver(device, None)
+            s.set_materials(lam.materials)
+            s.set_mesh(lam)
+            s.set_dirichlet(lam.dir_dof, lam.dir_val)
+            for face, t in lam.traction:
+                s.set_traction(face, t)
+            self.solvers.append(s)
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        self.b = C.c_void_p()
+        sp = None
+        if stream is not None:
+            sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _check(self.lib, self.lib.gl_batch_create(C.byref(self.b), len(self.solvers), C.cast(arr, C.c_void_p), sp))
+
+    def setup(self, px=0, py=0, overlap=1, nev=8, tol=1e-10, max_iter=2000, precision=GL_PREC_FP64,
+              resid_period=50, sigma=0.0, eig_iters=0):
+        o = gl_opts(px=px, py=py, pz=1, overlap=overlap, nev=nev, max_iter=max_iter, precision=precision,
+                    resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters)
+        _check(self.lib, self.lib.gl_batch_setup(self.b, C.byref(o)))
+
+    def grid(self):
+        out = np.zeros(2 * len(self.solvers), dtype=np.int32)
+        _check(self.lib, self.lib.gl_batch_grid(self.b, _ptr(out)))
+        return out.reshape(-1, 2)
+
+    def solve(self, outs=None, check=True):
+        n = len(self.solvers)
+        if outs is None:
+            outs = [np.empty(s.n_dof) for s in self.solvers]
+        ptrs = (C.c_void_p * n)(*[_ptr(o).value for o in outs])
+        infos = (gl_info * n)()
+        rc = self.lib.gl_batch_solve(self.b, C.cast(ptrs, C.c_void_p), C.cast(infos, C.c_void_p))
+        if check:
+            _check(self.lib, rc)
+        return outs, [infos[i].as_dict() for i in range(n)]
+
+    def close(self):
+        if self.b:
+            self.lib.gl_batch_destroy(self.b)
+            self.b = C.c_void_p()
+        for s in self.solvers:
+            s.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
