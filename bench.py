@@ -199,6 +199,20 @@ def run_batch(args):
     b.close()
 
 
+def aggregate_ranks(ms, units, world, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and the
+    sum of the work units of all ranks (no collective touches the solve itself)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms, float(units)], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return mx[0].item(), tt[1].item()
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -278,14 +292,7 @@ def main():
         barrier()
     launches = s.kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1)
-    t_max = ms
-    units = info["n_free"] * iters
-    if world > 1:
-        tt = torch.tensor([ms, float(units)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max, units = mx[0].item(), tt[1].item()
+    t_max, units = aggregate_ranks(ms, info["n_free"] * iters, world, dev)
     value = units / (t_max / 1e3)
 
     # end to end through the public API with host buffers (pinned f in, u out)

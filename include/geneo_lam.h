@@ -124,6 +124,10 @@ typedef struct {
     int64_t n_free;
     int n_coarse;            /* coarse-space dimension sum_j m_j */
     int64_t factor_nnz;      /* stored entries of all local factors */
+    int n_coarse_dropped;    /* coarse columns left out of K_0's Cholesky as
+                                linearly dependent (pivot <= 1e-10 with K_0
+                                scaled to unit diagonal), e.g. two subdomains
+                                that coincide on a narrow laminate */
 } gl_info;
 
 /* Context on CUDA device `device`; `cuda_stream` is a cudaStream_t (or NULL). */
@@ -164,6 +168,17 @@ int gl_solve(gl_ctx *ctx, const double *f, double *u, gl_info *info);
  * be NULL); peak_s33 (may be NULL) = the maximum of s33 over the isotropic
  * resin-interface elements. */
 int gl_stress(gl_ctx *ctx, const double *u, double *s33, double *t13, double *peak_s33);
+
+/* Quadratic damage-onset criterion (Section 3, Eq. eq-Camanho), per element:
+ *   F = sqrt((max(sigma_r, 0)/s33)^2 + (tau_rs/s13)^2 + (tau_rl/s13)^2)
+ * from the element-centre stresses in the local (s, l, r) frame, applied in
+ * the isotropic resin interfaces only (F = 0 elsewhere).  The paper's
+ * allowables are s33 = 61 MPa and s13 = 97 MPa.  F (n_elem, may be NULL);
+ * peak (may be NULL) = the largest F; peak_elem (may be NULL) = its element
+ * (ties within about 1e-5 relative may resolve to either element).  At most
+ * 16,777,215 elements. */
+int gl_failure_index(gl_ctx *ctx, const double *u, double s33_allow, double s13_allow, double *F, double *peak,
+                     int64_t *peak_elem);
 
 /* Gradients with respect to the per-element misalignment angles theta_e
  * (adjoint method; the objective is any function of the centre stresses).
@@ -211,7 +226,7 @@ int gl_geneo_eigenvalues(gl_ctx *ctx, double *lambda, int capacity, int *count);
  * gl_batch_create: n contexts with materials, mesh, Dirichlet data and
  *   tractions set (no gl_setup needed); they must live on one device and
  *   stay alive while the batch exists; their stream is replaced by the
- *   batch's.  cuda_stream may be NULL (the batch creates a non-blocking
+ *   batch's until gl_batch_destroy gives each its own back.  cuda_stream may be NULL (the batch creates a non-blocking
  *   stream; graph capture cannot use the legacy default stream).
  * gl_batch_setup: opts as for gl_setup except px, py: <= 0 selects, per
  *   laminate, the in-plane subdomain grid (px, py, 1) with 8 <= px py <= 64

@@ -13,7 +13,7 @@ Paper passages followed:
   * Section 3, the map after Eq. (eq-f): curved corner geometry
     x = L + r sin(pi s/2), y = l, z = r cos(pi s/2).
 
-Readings where the paper is silent (also listed in the design doc):
+Readings where the paper is silent:
   * Voigt order (11, 22, 33, 23, 13, 12) with engineering shear strains;
   * ply angle phi rotates about the laminate normal r, misalignment theta about
     the width axis l, then the curved frame rotates about l by the arc angle at
@@ -430,3 +430,19 @@ def stress_slr(mesh, u):
         s33[e] = Sl[2, 2]
         t13[e] = Sl[0, 2]
     return s33, t13
+
+
+def failure_index(mesh, u, s33=61.0, s13=97.0):
+    """Quadratic damage-onset criterion (Section 3, Eq. eq-Camanho) per element.
+
+    F = sqrt((max(sigma_r, 0)/s33)^2 + (tau_rs/s13)^2 + (tau_rl/s13)^2) from the
+    centre stress in the local (s, l, r) frame, evaluated in the isotropic
+    resin interfaces only (0 elsewhere); allowables s33 = 61 MPa, s13 = 97 MPa.
+    """
+    S = element_stress_centre(mesh, u)
+    F = np.zeros(mesh.n_elem)
+    for e in np.nonzero(mesh.is_resin)[0]:
+        Rf = rot_width(mesh.psi[e])
+        Sl = Rf.T @ S[e] @ Rf
+        F[e] = np.sqrt((max(Sl[2, 2], 0.0) / s33) ** 2 + (Sl[0, 2] / s13) ** 2 + (Sl[1, 2] / s13) ** 2)
+    return F

@@ -15,7 +15,7 @@ iterative solvers", and Fig. domaindecomp / Fig. eig):
   * two-level additive Schwarz = coarse correction + sum of local solves.
 
 Readings (the paper defers the GenEO details to its reference [geneo2]; this
-restates the standard published construction, also listed in the design doc):
+restates the standard published construction):
   * element boxes from a near-equal split of each index range (the first
     n % p boxes get one extra element), grown by `overlap` element layers;
   * V_j^N = free DOFs of the closed subdomain; artificial-boundary DOFs are
@@ -28,6 +28,9 @@ restates the standard published construction, also listed in the design doc):
     smallest lambda; solved through the definite pencil
     B p = mu (A_j^N + sigma B_j) p, lambda = 1/mu - sigma;
   * coarse basis Z = [R_j^T Xi_j p_j^k], K_0 = Z^T K Z, dense Cholesky;
+    columns that are linearly dependent on earlier ones (Cholesky pivot of
+    K_0 scaled to unit diagonal <= 1e-10, e.g. from two subdomains that
+    coincide on a narrow laminate) are left out of Z;
   * M^{-1} = Z K_0^{-1} Z^T + sum_j R_j^T A_j^{-1} R_j (additive);
   * PCG from x_0 = 0, stop when ||r_k||_2 / ||r_0||_2 <= tol.
 """
@@ -145,6 +148,33 @@ def geneo_eigs(AN, xi, nev, sigma=1e-2, method="arpack"):
     return lam[order], P[:, order]
 
 
+COARSE_DROP_TOL = 1e-10
+
+
+def independent_columns(K0, tol=COARSE_DROP_TOL):
+    """Columns kept by a Cholesky factorisation of K0 scaled to unit diagonal
+    that leaves out every column whose pivot is <= tol in magnitude (a column
+    in the span of the earlier ones, or a zero column).  Plain column-by-column
+    Cholesky in index order; raises on a negative pivot beyond tol."""
+    d = np.diag(K0).astype(float)
+    scale = np.zeros_like(d)
+    scale[d > 0] = 1.0 / np.sqrt(d[d > 0])
+    A = K0 * scale[:, None] * scale[None, :]
+    n = A.shape[0]
+    L = np.zeros_like(A)
+    keep = []
+    for j in range(n):
+        v = A[j, j] - L[j, :j] @ L[j, :j]
+        if abs(v) <= tol:
+            continue                      # column j stays out of the factor
+        if v < 0.0:
+            raise np.linalg.LinAlgError("coarse matrix not positive semi-definite")
+        L[j, j] = np.sqrt(v)
+        L[j + 1:, j] = (A[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+        keep.append(j)
+    return np.array(keep, dtype=np.int64)
+
+
 class GenEO:
     """Two-level additive Schwarz preconditioner with a GenEO coarse space."""
 
@@ -157,6 +187,7 @@ class GenEO:
             self.local.append(spla.splu(dec.dirichlet_matrix(s)))
         self.coarse = coarse
         self.eigvals = []
+        self.n_dropped = 0
         if coarse:
             cols, rows, vals = [], [], []
             c = 0
@@ -173,8 +204,13 @@ class GenEO:
                     c += 1
             self.Z = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                    shape=(nf, c))
-            self.K0 = (self.Z.T @ (Kff @ self.Z)).toarray()
-            self.K0 = 0.5 * (self.K0 + self.K0.T)
+            K0 = (self.Z.T @ (Kff @ self.Z)).toarray()
+            K0 = 0.5 * (K0 + K0.T)
+            keep = independent_columns(K0)
+            self.n_dropped = c - len(keep)
+            self.Z_all = self.Z
+            self.Z = self.Z[:, keep]
+            self.K0 = K0[np.ix_(keep, keep)]
             self.K0_chol = sla.cho_factor(self.K0, lower=True)
 
     def apply(self, r):

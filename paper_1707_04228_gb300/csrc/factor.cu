@@ -218,7 +218,7 @@ __global__ void k_extend_add(const int *__restrict__ children, const FrontDesc *
 // Diagonal block Cholesky (kb <= 32) of each front at pivot offset k0.
 template <class T>
 __global__ void k_potrf(const int *__restrict__ fronts, const FrontDesc *__restrict__ D, T *__restrict__ ws, int k0,
-                        int *__restrict__ err) {
+                        int *__restrict__ err, T drop, int *__restrict__ drops) {
     const FrontDesc d = D[fronts[blockIdx.x]];
     if (k0 >= d.p) return;
     const int kb = min(NB, d.p - k0), f = d.p + d.q;
@@ -232,15 +232,21 @@ __global__ void k_potrf(const int *__restrict__ fronts, const FrontDesc *__restr
     for (int j = 0; j < kb; ++j) {
         if (threadIdx.x == 0) {
             T v = a[j][j];
-            if (!(v > T(0))) {
-                atomicExch(err, 1);
-                v = T(1);
+            if (drop > T(0) && fabs(v) <= drop) {
+                // dependent column (drop mode): zero pivot, the column leaves the factor
+                atomicAdd(drops, 1);
+                a[j][j] = T(0);
+            } else {
+                if (!(v > T(0))) {
+                    atomicExch(err, 1);
+                    v = T(1);
+                }
+                a[j][j] = sqrt(v);
             }
-            a[j][j] = sqrt(v);
         }
         __syncthreads();
         T djj = a[j][j];
-        for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) a[i][j] /= djj;
+        for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) a[i][j] = djj != T(0) ? a[i][j] / djj : T(0);
         __syncthreads();
         for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
             int i = idx % kb, k = idx / kb;
@@ -280,7 +286,7 @@ __global__ void k_trsm(const int *__restrict__ fronts, const FrontDesc *__restri
 #pragma unroll
             for (int i = 0; i < NB; ++i)
                 if (i < j) v -= x[i] * l[j][i];
-            x[j] = v / l[j][j];
+            x[j] = l[j][j] != T(0) ? v / l[j][j] : T(0);   // zero pivot: a dropped column
         }
     }
 #pragma unroll
@@ -358,7 +364,8 @@ __global__ void k_copy_panel(const int *__restrict__ fronts, const FrontDesc *__
 }
 
 static void partial_cholesky_level(const int *d_fronts, int n_fronts, const FrontDesc *d_fr, int max_p, int max_f,
-                                   void *ws, bool fp32, int *d_err, cudaStream_t s) {
+                                   void *ws, bool fp32, int *d_err, cudaStream_t s, double drop = 0.0,
+                                   int *d_drops = nullptr) {
     for (int k0 = 0; k0 < max_p; k0 += NB) {
         // upper bounds over the level's fronts (a front's last pivot block may be short)
         int rows = std::max(1, max_f - k0);
@@ -367,11 +374,11 @@ static void partial_cholesky_level(const int *d_fronts, int n_fronts, const Fron
         int tiles = std::max(1, nt * (nt + 1) / 2);
         dim3 gt(n_fronts, (rows + 127) / 128), gs(n_fronts, tiles);
         if (fp32) {
-            k_potrf<float><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k0, d_err);
+            k_potrf<float><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k0, d_err, (float)drop, d_drops);
             k_trsm<float><<<gt, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k0);
             k_syrk<float><<<gs, 256, 0, s>>>(d_fronts, d_fr, (float *)ws, k0);
         } else {
-            k_potrf<double><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (double *)ws, k0, d_err);
+            k_potrf<double><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (double *)ws, k0, d_err, drop, d_drops);
             k_trsm<double><<<gt, 128, 0, s>>>(d_fronts, d_fr, (double *)ws, k0);
             k_syrk<double><<<gs, 256, 0, s>>>(d_fronts, d_fr, (double *)ws, k0);
         }
@@ -724,32 +731,49 @@ template void scatter_add_local<float>(const FactorPlan &, const float *, double
 // ----------------------------------------------------------------- dense (coarse) inverse
 
 // K^{-1} of a dense SPD matrix through the same partial Cholesky: factoring the
-// p = n pivots of the 2n x 2n front [[A, I], [I, 0]] leaves the Schur
-// complement 0 - I A^{-1} I = -A^{-1} in the trailing block.
+// p = n pivots of the 2n x 2n front [[A_s, I], [I, 0]] leaves the Schur
+// complement 0 - I A_s^{-1} I = -A_s^{-1} in the trailing block, where
+// A_s = D A D is A scaled to unit diagonal (D = diag(A)^{-1/2}); then
+// A^{-1} = D A_s^{-1} D.  With drop > 0 a pivot of |v| <= drop (on the unit
+// diagonal scale) marks its column as linearly dependent on the earlier ones:
+// the column is left out of the factor, its row and column of the result are
+// zero, and the result is the inverse of A on the kept columns -- a
+// generalised inverse of A when the dropped columns lie in the span of the
+// kept ones (a zero column of A has a zero scaled pivot and is dropped too).
+__device__ __forceinline__ double unit_diag_scale(const double *A, int n, int64_t i) {
+    const double d = A[i + i * (int64_t)n];
+    return d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+}
+
 __global__ void k_aug_init(const double *__restrict__ A, int n, double *__restrict__ F) {
     const int64_t m = 2 * (int64_t)n;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < m * m; idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = idx % m, j = idx / m;
         double v = 0.0;
-        if (i < n && j < n) v = A[i + j * n];
-        else if (j < n && i - n == j) v = 1.0;
+        if (i < n && j < n) {
+            const double di = unit_diag_scale(A, n, i), dj = unit_diag_scale(A, n, j);
+            v = (di == 0.0 || dj == 0.0) ? 0.0 : A[i + j * n] * di * dj;
+        } else if (j < n && i - n == j) {
+            v = 1.0;
+        }
         F[idx] = v;
     }
 }
 
-__global__ void k_extract_inv(const double *__restrict__ F, int n, double *__restrict__ Ainv) {
+__global__ void k_extract_inv(const double *__restrict__ A, const double *__restrict__ F, int n,
+                              double *__restrict__ Ainv) {
     const int64_t m = 2 * (int64_t)n;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = idx % n, j = idx / n;
         int64_t a = i > j ? i : j, b = i > j ? j : i;   // lower triangle of the trailing block
-        Ainv[idx] = -F[(n + a) + (n + b) * m];
+        Ainv[idx] = -F[(n + a) + (n + b) * m] * unit_diag_scale(A, n, i) * unit_diag_scale(A, n, j);
     }
 }
 
-void dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s) {
+int dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s, double drop) {
     DBuf<FrontDesc> d;
-    DBuf<int> idx;
+    DBuf<int> idx, drops;
     FrontDesc f{};
     f.p = n;
     f.q = n;
@@ -757,14 +781,19 @@ void dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_
     f.parent = -1;
     d.upload(std::vector<FrontDesc>{f}, s);
     idx.upload(std::vector<int>{0}, s);
+    drops.alloc(1);
+    drops.zero(s);
     DBuf<double> F;
     F.alloc((size_t)4 * n * n);
     k_aug_init<<<1024, 256, 0, s>>>(A, n, F.p);
     GL_CUDA(cudaGetLastError());
-    partial_cholesky_level(idx.p, 1, d.p, n, 2 * n, F.p, false, d_err, s);
-    k_extract_inv<<<1024, 256, 0, s>>>(F.p, n, Ainv);
+    partial_cholesky_level(idx.p, 1, d.p, n, 2 * n, F.p, false, d_err, s, drop, drops.p);
+    k_extract_inv<<<1024, 256, 0, s>>>(A, F.p, n, Ainv);
     GL_CUDA(cudaGetLastError());
+    int h = 0;
+    GL_CUDA(cudaMemcpyAsync(&h, drops.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     GL_CUDA(cudaStreamSynchronize(s));
+    return h;
 }
 
 // y = A x for symmetric A (n x n, column-major): warp per output reads column i.

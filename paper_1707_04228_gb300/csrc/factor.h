@@ -73,8 +73,10 @@ void scatter_add_local(const FactorPlan &P, const T *xl, double *z, cudaStream_t
 void dense_symv_blocks(const double *A, const int64_t *aoff, const int *voff, const int *nb, int nblk, int total,
                        const double *x, double *y, cudaStream_t s);
 // A^{-1} (n x n, column-major) of a dense SPD A by Cholesky of the front
-// [[A, I], [I, 0]] (Schur complement -A^{-1}); y = A x for symmetric A.
-void dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s);
+// [[D A D, I], [I, 0]] (D = diag(A)^{-1/2}; Schur complement -(D A D)^{-1}).
+// drop > 0: columns whose pivot on the unit-diagonal scale is <= drop are left
+// out (zero rows and columns in Ainv); returns how many were dropped.
+int dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s, double drop = 0.0);
 void dense_symv(const double *A, int n, const double *x, double *y, cudaStream_t s);
 
 }  // namespace gl

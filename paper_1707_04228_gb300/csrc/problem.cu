@@ -14,6 +14,13 @@ namespace gl {
 
 namespace {
 
+// Coarse columns whose Cholesky pivot of the unit-diagonal-scaled K_0 falls to
+// 1e-10 or below (the column lies within an angle of about 1e-5, in the K
+// inner product, of the span of the earlier ones) are dropped as dependent:
+// this happens when two subdomains coincide (a box grown by the overlap to the
+// whole extent of a narrow laminate) or when Xi_j p vanishes.
+constexpr double COARSE_DROP_TOL = 1e-10;
+
 template <class F>
 void parallel_for(int n, F fn) {
     int nt = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
@@ -304,6 +311,8 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
     local_K_apply(PN, E, P.C, P.geo, nullptr, out.Z.p, KZ.p, nev, s);
     out.koff.clear();
     out.kvoff.clear();
+    out.n_dropped = 0;
+    out.part_dropped.assign(P.parts.size(), 0);
     out.kn.clear();
     int64_t ktot = 0;
     for (const Part &pt : P.parts) {
@@ -341,7 +350,8 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
             k_scatter_cols<<<256, 256, 0, s>>>(PN.d_gdof.p, oj, nj, KZ.p, oj * nev, nev, G.p, Np, pt.dof_off, 1);
             GL_CUDA(cudaGetLastError());
         }
-        dense_inverse(K0.p, n0p, out.Kinv.p + out.koff[ip], P.d_err, s);
+        out.part_dropped[ip] = dense_inverse(K0.p, n0p, out.Kinv.p + out.koff[ip], P.d_err, s, COARSE_DROP_TOL);
+        out.n_dropped += out.part_dropped[ip];
         check_err(P, "coarse Cholesky");
     }
     out.d_koff.upload(out.koff, s);

@@ -345,6 +345,8 @@ void setup(gl_ctx *c, const gl_opts &o) {
     if (std::getenv("GL_VERBOSE"))
         std::fprintf(stderr, "[gl] GenEO subspace iterations (max over groups): %d\n", c->co.eig_iters);
     stamp(c, "GenEO coarse space + K0");
+    if (c->co.n_dropped && std::getenv("GL_VERBOSE"))
+        std::fprintf(stderr, "[gl]   %d dependent coarse columns dropped\n", c->co.n_dropped);
     // work vectors
     const int64_t N = m.n_dof;
     for (DBuf<double> *b : {&c->x, &c->r, &c->z, &c->p, &c->q, &c->ud, &c->fe}) b->alloc(N);
@@ -478,6 +480,7 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info, bool homogeneou
         info->ms_solve = ms;
         info->n_free = c->n_free;
         info->n_coarse = c->co.n0;
+        info->n_coarse_dropped = c->co.n_dropped;
         info->factor_nnz = c->PD.l_size;
     }
     if (status != GL_OK) {
@@ -495,6 +498,7 @@ struct gl_batch {
     cudaStream_t stream = 0;
     bool own_stream = false, ready = false;
     std::vector<gl_ctx *> items;
+    std::vector<cudaStream_t> item_streams;   // each laminate's own stream, given back on destruction
     gl_opts opts{};
     Problem prob;
     FactorPlan PD;
@@ -520,6 +524,7 @@ struct gl_batch {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         if (h_active) cudaFreeHost(h_active);
+        for (size_t i = 0; i < item_streams.size(); ++i) items[i]->stream = item_streams[i];
         if (own_stream) cudaStreamDestroy(stream);
     }
     SegScalars seg() {
@@ -875,6 +880,7 @@ void batch_solve(gl_batch *b, double *const *u, gl_info *infos) {
             in.ms_solve = ms;
             in.n_free = b->n_free[i];
             in.n_coarse = (int)(b->co.n0 ? b->co.kn[i] : 0);
+            in.n_coarse_dropped = b->co.part_dropped.empty() ? 0 : b->co.part_dropped[i];
             in.factor_nnz = b->PD.l_size;
         }
     }
@@ -1158,6 +1164,34 @@ int gl_apply_prec(gl_ctx *c, const double *r, double *z) {
     });
 }
 
+int gl_failure_index(gl_ctx *c, const double *u, double s33_allow, double s13_allow, double *F, double *peak,
+                     int64_t *peak_elem) {
+    return guard([&] {
+        require_ctx(c);
+        if (!c->ready) fail(GL_ERR_STATE, "gl_failure_index before gl_setup");
+        GL_REQUIRE(u, "null displacement");
+        GL_REQUIRE(s33_allow > 0 && s13_allow > 0, "allowables must be positive");
+        const MeshHost &m = c->m;
+        GL_REQUIRE(m.n_elem < (int64_t)1 << 24, "gl_failure_index: at most 16,777,215 elements");
+        cudaStream_t s = c->stream;
+        DBuf<double> du, dF;
+        DBuf<unsigned long long> best;
+        du.alloc(m.n_dof);
+        to_device(du.p, u, m.n_dof, s);
+        dF.alloc(m.n_elem);
+        best.alloc(1);
+        launch_failure(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_resin.p, du.p, s33_allow, s13_allow, dF.p, best.p, s);
+        g_launches += 1;
+        unsigned long long key = 0;
+        GL_CUDA(cudaMemcpyAsync(&key, best.p, sizeof(key), cudaMemcpyDeviceToHost, s));
+        GL_CUDA(cudaStreamSynchronize(s));
+        const int64_t e = (int64_t)(key & 0xFFFFFF);
+        if (peak_elem) *peak_elem = e;
+        if (peak) from_device(peak, dF.p + e, 1, s);
+        if (F) from_device(F, dF.p, m.n_elem, s);
+    });
+}
+
 int gl_set_theta(gl_ctx *c, const double *theta_e) {
     return guard([&] {
         require_ctx(c);
@@ -1296,6 +1330,7 @@ int gl_batch_create(gl_batch **out, int n, gl_ctx *const *items, void *cuda_stre
                 GL_REQUIRE(items[i]->device == b->device, "all laminates of a batch must be on one device");
                 for (int j = 0; j < i; ++j) GL_REQUIRE(items[j] != items[i], "a laminate appears twice in the batch");
                 b->items.push_back(items[i]);
+                b->item_streams.push_back(items[i]->stream);
             }
             GL_CUDA(cudaSetDevice(b->device));
             if (cuda_stream) {

@@ -48,7 +48,8 @@ class gl_opts(C.Structure):
 class gl_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("rel_resid", C.c_double),
                 ("rel_resid_true", C.c_double), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
-                ("n_free", C.c_int64), ("n_coarse", C.c_int), ("factor_nnz", C.c_int64)]
+                ("n_free", C.c_int64), ("n_coarse", C.c_int), ("factor_nnz", C.c_int64),
+                ("n_coarse_dropped", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +85,8 @@ SIGNATURES = {
     "gl_apply_K": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_apply_prec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_geneo_eigenvalues": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "gl_failure_index": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_int64)]),
     "gl_set_theta": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gl_stress_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(gl_info)]),
@@ -260,6 +263,14 @@ class Solver:
         out = np.empty(self.n_dof) if out is None else out
         _check(self.lib, self.lib.gl_apply_prec(self.ctx, _ptr(r), _ptr(out)))
         return out
+
+    def failure_index(self, u, s33=61.0, s13=97.0, F=None):
+        """Quadratic damage-onset criterion per element; returns (F, peak, peak element)."""
+        F = np.empty(self.n_elem) if F is None else F
+        peak = np.zeros(1)
+        elem = C.c_int64()
+        _check(self.lib, self.lib.gl_failure_index(self.ctx, _ptr(u), s33, s13, _ptr(F), _ptr(peak), C.byref(elem)))
+        return F, float(peak[0]), elem.value
 
     def set_theta(self, theta):
         t = theta if hasattr(theta, "data_ptr") else np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)

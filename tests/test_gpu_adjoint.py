@@ -17,8 +17,10 @@ pytestmark = pytest.mark.gpu
 
 
 def corner():
-    lam = inputs.corner_mini(n_arc=6, n_limb=1, n_width=3, nel_layer=1, angles=(0, 90, 45), nsub=(4, 1, 1), nev=8,
-                             limb_L=3.0, width=3.0, wrinkle_w=1.0)
+    """The 8 x 6 x 14 curved laminate (19,227 DOF): the arc of the corner family with
+    [0/90]s plies and resin interfaces, 2 elements per layer, a 10-degree wrinkle."""
+    lam = inputs.corner_mini(n_arc=8, n_limb=0, n_width=6, nel_layer=2, angles=(0, 90), nsub=(4, 2, 1), nev=8,
+                             width=6.0, wrinkle_w=1.0)
     lam.tol = 1e-12
     return lam
 

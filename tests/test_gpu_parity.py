@@ -186,3 +186,34 @@ def test_single_subdomain_is_a_direct_solve(lib_mod):
     assert info["iters"] <= 2
     u_ref = fem.System(fem.Mesh(lam)).direct()
     assert rel(u, u_ref) <= 1e-9
+
+
+def test_failure_index_matches_oracle(lib_mod):
+    """Eq. eq-Camanho on the resin interfaces of a loaded curved corner."""
+    lam = small_curved()
+    mesh = fem.Mesh(lam)
+    u = fem.System(mesh).direct()
+    s = lib_mod.Solver.from_laminate(lam)
+    F, peak, e = s.failure_index(u)
+    ref = fem.failure_index(mesh, u)
+    assert rel(F, ref) <= 1e-11
+    assert np.all(F[~mesh.is_resin] == 0.0)
+    assert abs(peak - ref.max()) <= 1e-11 * ref.max() + 2e-5 * ref.max()
+    assert F[e] == peak and mesh.is_resin[e]
+
+
+def test_coincident_subdomains_drop_coarse_columns(lib_mod):
+    """Two elements across the width split in two with overlap 1: each pair of
+    subdomains coincides and their GenEO vectors span the same space (up to the
+    eigensolver's convergence), so K_0 is singular.  The dependent columns are
+    dropped (at most the 2 x 6 of the oracle, which finds the exact duplicates)
+    and the solve still reaches the direct solution."""
+    lam = inputs.corner_mini(n_arc=4, n_limb=1, n_width=2, nel_layer=1, angles=(0, 90), nsub=(2, 2, 1), nev=6,
+                             limb_L=2.0, width=2.0)
+    mesh = fem.Mesh(lam)
+    u_ref = fem.System(mesh).direct()
+    s = lib_mod.Solver.from_laminate(lam, px=2, py=2, pz=1, nev=6, tol=1e-12)
+    u, info = s.solve()
+    assert info["status"] == 0
+    assert 0 < info["n_coarse_dropped"] <= 12
+    assert rel(u, u_ref) <= 1e-8

@@ -9,6 +9,7 @@ import os
 
 import numpy as np
 import pytest
+from scipy.linalg import solve as sla_solve
 
 from oracle import fem, geneo
 from paper_1707_04228_gb300 import inputs
@@ -373,6 +374,46 @@ def _strip(ns):
     return lam
 
 
+def test_independent_columns_match_rank():
+    """Dependent-column dropping keeps a basis of the column space: a duplicated
+    column, a linear combination and a zero column go; the count equals the
+    rank from numpy's SVD and the kept Gram block is positive definite."""
+    rng = np.random.default_rng(8)
+    G = rng.standard_normal((60, 12))
+    G[:, 5] = G[:, 1]
+    G[:, 8] = 2.0 * G[:, 0] - 3.0 * G[:, 3]
+    G[:, 10] = 0.0
+    K0 = G.T @ G
+    keep = geneo.independent_columns(K0)
+    assert list(keep) == [j for j in range(12) if j not in (5, 8, 10)]
+    assert len(keep) == np.linalg.matrix_rank(G)
+    np.linalg.cholesky(K0[np.ix_(keep, keep)])
+
+
+def test_coincident_subdomains_drop_coarse_columns():
+    """A laminate two elements wide split in two across its width with overlap 1:
+    both subdomains of each pair grow to the full width and coincide, so half
+    of their GenEO vectors are dependent.  The dropped columns lie in the span
+    of the kept ones (the K-orthogonal coarse projector reproduces them) and
+    PCG still converges to the direct solution."""
+    lam = inputs.corner_mini(n_arc=4, n_limb=1, n_width=2, nel_layer=1, angles=(0, 90), nsub=(2, 2, 1), nev=6,
+                             limb_L=2.0, width=2.0)
+    sysm = fem.System(fem.Mesh(lam))
+    dec = geneo.Decomposition(sysm, 2, 2, 1, 1)
+    sets = [tuple(np.sort(s.VN)) for s in dec.subs]
+    pairs = sum(1 for i in range(len(sets)) for j in range(i) if sets[i] == sets[j])
+    assert pairs == 2
+    P = geneo.GenEO(dec, 6, eig_method="dense")
+    assert P.n_dropped == 6 * pairs
+    K = sysm.Kff
+    Z, Za = P.Z.toarray(), P.Z_all.toarray()
+    proj = Z @ sla_solve(P.K0, Z.T @ (K @ Za))
+    assert np.abs(proj - Za).max() <= 1e-8 * np.abs(Za).max()
+    u, it, hist, _, _ = geneo.solve(lam, system=sysm, px=2, py=2, pz=1, nev=6, tol=1e-12)
+    ud = sysm.direct()
+    assert np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
+
+
 def test_geneo_iterations_flat_while_one_level_grows():
     """Section 2.3: GenEO iterations stay roughly constant as subdomains are added,
     one-level Schwarz iterations grow (the paper reports ~40 against ~400)."""
@@ -414,3 +455,20 @@ def test_oracle_adjoint_gradient_matches_central_differences():
         fd = (adjoint.objective_at(lam, tp, mask, 8) - adjoint.objective_at(lam, tm, mask, 8)) / (2 * h)
         assert abs(fd - grad[e]) <= 1e-6 * np.abs(grad).max()
     assert np.all(grad[mesh.is_resin & ~mask] == 0.0)
+
+
+def test_failure_index_uniform_stress_closed_form():
+    """Eq. eq-Camanho on a resin block under a uniform strain: sigma = C eps is known
+    in closed form, so F = sqrt((max(s_zz,0)/61)^2 + (s_xz/97)^2 + (s_yz/97)^2)."""
+    iso = dict(kind="iso", E=10000.0, nu=0.35)
+    lam = block(2, 2, [(2, 1.0, 0, 0.0)], sx=2.0, sy=2.0, mats=[iso])
+    mesh = fem.Mesh(lam)
+    for sign in (1.0, -1.0):
+        eps = np.array([[1e-4, 2e-4, 3e-4], [2e-4, -1e-4, 5e-4], [3e-4, 5e-4, sign * 4e-4]])
+        u = (mesh.X @ eps.T).ravel()
+        Cv = fem.isotropic_C(**iso)
+        ev = np.array([eps[0, 0], eps[1, 1], eps[2, 2], 2 * eps[1, 2], 2 * eps[0, 2], 2 * eps[0, 1]])
+        s = Cv @ ev
+        F_exact = np.sqrt((max(s[2], 0.0) / 61.0) ** 2 + (s[4] / 97.0) ** 2 + (s[3] / 97.0) ** 2)
+        F = fem.failure_index(mesh, u)
+        assert np.allclose(F, F_exact, rtol=1e-12)
