@@ -169,7 +169,7 @@ int gl_solve(gl_ctx *ctx, const double *f, double *u, gl_info *info);
  * resin-interface elements. */
 int gl_stress(gl_ctx *ctx, const double *u, double *s33, double *t13, double *peak_s33);
 
-/* Quadratic damage-onset criterion (Section 3, Eq. eq-Camanho), per element:
+/* Quadratic damage-onset criterion (Section 3.2, Eq. eq-Camanho), per element:
  *   F = sqrt((max(sigma_r, 0)/s33)^2 + (tau_rs/s13)^2 + (tau_rl/s13)^2)
  * from the element-centre stresses in the local (s, l, r) frame, applied in
  * the isotropic resin interfaces only (F = 0 elsewhere).  The paper's

@@ -433,7 +433,7 @@ def stress_slr(mesh, u):
 
 
 def failure_index(mesh, u, s33=61.0, s13=97.0):
-    """Quadratic damage-onset criterion (Section 3, Eq. eq-Camanho) per element.
+    """Quadratic damage-onset criterion (Section 3.2, Eq. eq-Camanho) per element.
 
     F = sqrt((max(sigma_r, 0)/s33)^2 + (tau_rs/s13)^2 + (tau_rl/s13)^2) from the
     centre stress in the local (s, l, r) frame, evaluated in the isotropic

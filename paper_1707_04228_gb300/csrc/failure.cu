@@ -1,4 +1,4 @@
-// Quadratic damage-onset criterion of Section 3 (Eq. eq-Camanho):
+// Quadratic damage-onset criterion of Section 3.2 (Eq. eq-Camanho):
 //   F = sqrt((sigma_r^+ / s33)^2 + (tau_rs / s13)^2 + (tau_rl / s13)^2),
 // sigma_r^+ = max(sigma_rr, 0), applied in the isotropic resin interfaces only
 // (zero elsewhere), with the stresses recovered at the element centre and
