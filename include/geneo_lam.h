@@ -169,6 +169,33 @@ int gl_solve(gl_ctx *ctx, const double *f, double *u, gl_info *info);
  * resin-interface elements. */
 int gl_stress(gl_ctx *ctx, const double *u, double *s33, double *t13, double *peak_s33);
 
+/* Stress recovery that allocates nothing.  The paper has no counterpart: this
+ * entry point is for callers that cannot allocate device memory while they
+ * run -- a host framework that has handed nearly all device memory to its own
+ * caching pool (the local factors leave little free), a latency-bound loop in
+ * which cudaMalloc or cudaFree would synchronise the device and stall the
+ * other streams, or a deployment whose device footprint must stay fixed once
+ * the library is loaded.  It computes what gl_stress computes, with these
+ * differences:
+ *   - u (N entries), s33 and t13 (n_elem each) and peak_s33 (one double, may
+ *     be NULL) must be device memory of the context's device, allocated by
+ *     the caller; anything else is rejected with GL_ERR_INVALID_ARG;
+ *   - it calls no cudaMalloc, cudaFree or allocating library routine: the
+ *     partial maxima of the resin peak live in a fixed array of 16,384
+ *     doubles (128 KB) inside the library, which every GPU that loads the
+ *     library holds until the process exits; meshes of more than 4,194,304
+ *     elements are rejected with GL_ERR_INVALID_ARG;
+ *   - the work is queued on the context's stream and the call returns without
+ *     waiting for it;
+ *   - the first call on a device looks up the array's device address and
+ *     caches it; make that first call before any stream capture begins;
+ *   - all calls on a device share the one array, which keeps the last call's
+ *     contents.  Each call writes every slot it reads before reading it, so
+ *     nothing has to be cleared between calls, but calls whose work overlaps
+ *     on the GPU (other streams, other contexts) race on it: order them on
+ *     one stream or synchronise between them. */
+int gl_stress_noalloc(gl_ctx *ctx, const double *u, double *s33, double *t13, double *peak_s33);
+
 /* Quadratic damage-onset criterion (Section 3.2, Eq. eq-Camanho), per element:
  *   F = sqrt((max(sigma_r, 0)/s33)^2 + (tau_rs/s13)^2 + (tau_rl/s13)^2)
  * from the element-centre stresses in the local (s, l, r) frame, applied in

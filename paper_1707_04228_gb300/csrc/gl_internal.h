@@ -153,6 +153,10 @@ void launch_stress(const MeshHost &m, const double *X, const double *C, const do
                    const double *u, double *s33, double *t13, cudaStream_t s);
 void launch_failure(const MeshHost &m, const double *X, const double *C, const double *psi_x, const uint8_t *resin,
                     const double *u, double s33a, double s13a, double *F, unsigned long long *best, cudaStream_t s);
+// Stress recovery into caller device buffers with the resin peak reduced
+// through a fixed file-scope device scratch (no device allocation).
+void stress_noalloc(const MeshHost &m, int device, const double *X, const double *C, const double *psi_x,
+                    const uint8_t *resin, const double *u, double *s33, double *t13, double *peak, cudaStream_t s);
 void launch_stress_vjp(const MeshHost &m, const double *X, const double *C, const double *psi_x,
                        const int *layer_of_ez, const int *layer_mat, const double *layer_angle, const double *theta,
                        const double *matC, const double *u, const double *w33, const double *w13, double *dJdu,

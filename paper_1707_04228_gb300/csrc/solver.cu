@@ -1139,6 +1139,26 @@ int gl_stress(gl_ctx *c, const double *u, double *s33, double *t13, double *peak
     });
 }
 
+int gl_stress_noalloc(gl_ctx *c, const double *u, double *s33, double *t13, double *peak) {
+    return guard([&] {
+        require_ctx(c);
+        if (!c->ready) fail(GL_ERR_STATE, "gl_stress_noalloc before gl_setup");
+        GL_REQUIRE(u && s33 && t13, "gl_stress_noalloc: u, s33 and t13 are required");
+        auto on_ctx_device = [&](const void *p) {
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == c->device;
+        };
+        GL_REQUIRE(on_ctx_device(u) && on_ctx_device(s33) && on_ctx_device(t13) && (!peak || on_ctx_device(peak)),
+                   "gl_stress_noalloc: every buffer must be device memory of the context's device");
+        stress_noalloc(c->m, c->device, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_resin.p, u, s33, t13, peak, c->stream);
+        g_launches += 1 + (peak ? 2 : 0);
+    });
+}
+
 int gl_apply_K(gl_ctx *c, const double *x, double *y) {
     return guard([&] {
         require_ctx(c);

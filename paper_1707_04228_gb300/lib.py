@@ -82,6 +82,7 @@ SIGNATURES = {
     "gl_rhs": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gl_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(gl_info)]),
     "gl_stress": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gl_stress_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_apply_K": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_apply_prec": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_geneo_eigenvalues": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
@@ -253,6 +254,15 @@ class Solver:
         peak = np.zeros(1)
         _check(self.lib, self.lib.gl_stress(self.ctx, _ptr(u), _ptr(s33), _ptr(t13), _ptr(peak)))
         return s33, t13, float(peak[0])
+
+    def stress_noalloc(self, u, s33, t13, peak=None):
+        """gl_stress_noalloc: u, s33, t13 and peak (or None) are caller-owned
+        device buffers (torch tensors or raw device addresses); nothing is
+        allocated and the call returns before the work on the context's stream
+        is done."""
+        def dptr(a):
+            return C.c_void_p(a) if isinstance(a, int) else _ptr(a)
+        _check(self.lib, self.lib.gl_stress_noalloc(self.ctx, dptr(u), dptr(s33), dptr(t13), dptr(peak)))
 
     def apply_K(self, x, out=None):
         out = np.empty(self.n_dof) if out is None else out
