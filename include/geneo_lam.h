@@ -289,6 +289,9 @@ typedef struct {
     int factor_levels;                   /* non-empty dissection levels (2 sweeps each) */
     int64_t n_elem, n_dof;
     int n_sub, n_coarse_dim;
+    int64_t factor_nonzeros;             /* entries of the lower-triangular factors
+                                            (sum over fronts of p(p+1)/2 + p q):
+                                            what the two sweeps read and multiply */
 } gl_profile_data;
 int gl_profile(gl_ctx *ctx, int enable);
 int gl_profile_read(gl_ctx *ctx, gl_profile_data *out);

@@ -27,6 +27,8 @@ constexpr int TILE = 64;      // trailing-update tile
 
 // ----------------------------------------------------------------- plan
 
+void sweep_smem_for_plan(int max_f);
+
 void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_t s) {
     P.n_sub = (int)subs.size();
     P.vec_off.clear();
@@ -79,6 +81,8 @@ void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_
     }
     P.n_local = voff;
     P.l_size = loff;
+    P.nnz = 0;
+    for (const FrontDesc &d : P.fr) P.nnz += (int64_t)d.p * (d.p + 1) / 2 + (int64_t)d.p * d.q;
     P.ws_max = 0;
     P.max_f = 0;
     for (auto &L : P.levels) {
@@ -107,6 +111,7 @@ void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_
     P.d_gdof.upload(P.h_gdof, s);
     P.d_vec_off.upload(P.vec_off, s);
     P.d_vec_len.upload(P.vec_len, s);
+    sweep_smem_for_plan(P.max_f);
     GL_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -386,6 +391,58 @@ static void partial_cholesky_level(const int *d_fronts, int n_fronts, const Fron
     }
 }
 
+// Partitioned-inverse form of the stored factor, used by the sweeps.  For
+// every block B of 32 consecutive pivots of a front (the last one may be
+// shorter): L[B,B] <- L[B,B]^{-1} (lower triangular) and, for every row i
+// below B in the front (later pivots and structure rows),
+// L[i,B] <- W[i,B] = L[i,B] L[B,B]^{-1}.  A forward step is then
+// y_B = L[B,B]^{-1} x_B and x_i -= W[i,B] x_B, a backward step
+// x_B = L[B,B]^{-T} y_B - W[i,B]^T x_i: plain products with no serial
+// triangular solve.  Computed in FP64 whatever the storage type.  One CTA per
+// (front, block); blocks are independent of one another.
+template <class T>
+__global__ void __launch_bounds__(256) k_block_inverse(const FrontDesc *__restrict__ D, T *__restrict__ L) {
+    const FrontDesc d = D[blockIdx.x];
+    const int jb = blockIdx.y * 32;
+    if (jb >= d.p) return;
+    const int kb = min(32, d.p - jb), f = d.p + d.q;
+    T *Lp = L + d.l_off;
+    __shared__ double Dk[32][33], Li[32][33];
+    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+        const int i = idx & 31, j = idx >> 5;
+        Dk[i][j] = (i < kb && j < kb && i >= j) ? (double)Lp[(jb + i) + (int64_t)(jb + j) * f] : 0.0;
+        Li[i][j] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < kb) {
+        // column j of the inverse by forward substitution on e_j
+        const int j = threadIdx.x;
+        Li[j][j] = 1.0 / Dk[j][j];
+        for (int i = j + 1; i < kb; ++i) {
+            double acc = 0.0;
+            for (int k = j; k < i; ++k) acc += Dk[i][k] * Li[k][j];
+            Li[i][j] = -acc / Dk[i][i];
+        }
+    }
+    __syncthreads();
+    for (int i = jb + kb + threadIdx.x; i < f; i += blockDim.x) {
+        double r[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) r[k] = k < kb ? (double)Lp[i + (int64_t)(jb + k) * f] : 0.0;
+#pragma unroll 1
+        for (int j = 0; j < kb; ++j) {
+            double w = 0.0;   // Li is lower triangular: the terms k < j vanish
+#pragma unroll
+            for (int k = 0; k < 32; ++k) w += r[k] * Li[k][j];
+            Lp[i + (int64_t)(jb + j) * f] = (T)w;
+        }
+    }
+    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+        const int i = idx & 31, j = idx >> 5;
+        if (i < kb && j < kb && i >= j) Lp[(jb + i) + (int64_t)(jb + j) * f] = (T)Li[i][j];
+    }
+}
+
 // Subdomains are factorised in consecutive groups whose two live levels of
 // dense fronts fit a workspace budget; inside a group every level is one set
 // of batched launches.
@@ -485,6 +542,13 @@ void numeric_factor(FactorPlan &P, const double *C, const double *geo, const dou
         GL_CUDA(cudaStreamSynchronize(s));   // the group's lists are released at the end of this scope
         j0 = j1;
     }
+    int max_p = 0;
+    for (const FrontDesc &d : P.fr) max_p = std::max(max_p, d.p);
+    if (!P.fr.empty() && max_p > 0) {
+        k_block_inverse<T><<<dim3((unsigned)P.fr.size(), (max_p + 31) / 32), 256, 0, s>>>(P.d_fr.p, L);
+        GL_CUDA(cudaGetLastError());
+        GL_CUDA(cudaStreamSynchronize(s));
+    }
 }
 
 template void numeric_factor<double>(FactorPlan &, const double *, const double *, const double *, double, double *,
@@ -494,49 +558,61 @@ template void numeric_factor<float>(FactorPlan &, const double *, const double *
 
 // ----------------------------------------------------------------- solves
 
-// Forward substitution for the fronts of one level: pivots y = L11^{-1} x_p,
-// then the structure rows x_s -= L21 y (atomic: sibling fronts share rows).
+// The sweeps read the partitioned-inverse form written by k_block_inverse.
+// Dynamic shared memory of both: the front's dense vector v (f x NR entries)
+// followed by a 32 x NR staging area (placed there, aliasing v's buffer, so
+// that its reads are not hoisted into registers).
+//
+// Forward substitution for the fronts of one level, one CTA per front: for
+// each block B of 32 pivots in turn, x_B is copied and L[B,B]^{-1} staged in
+// shared memory; warp 0 forms y_B = L[B,B]^{-1} x_B while all warps update the
+// rows below, x_i -= W[i,B] x_B, one row per thread.  No serial triangular
+// solve remains.  Structure rows are added into the ancestors' entries
+// atomically (siblings share rows).
 template <class T, int NR>
 __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
                                              const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
                                              int kcols, int c0) {
     extern __shared__ unsigned char smraw[];
-    T *v = reinterpret_cast<T *>(smraw);
     const FrontDesc d = D[fronts[blockIdx.x]];
     const int p = d.p, f = d.p + d.q, n = d.vlen;
+    T *v = reinterpret_cast<T *>(smraw);
+    T *xb = v + (int64_t)f * NR;   // the copy of x_B (32 x NR)
+    __shared__ T dblk[32][33];      // L[B,B]^{-1}, lower triangle
     T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
     for (int i = threadIdx.x; i < f; i += blockDim.x)
 #pragma unroll
         for (int r = 0; r < NR; ++r) v[i + r * f] = i < p ? xs[(int64_t)r * n + d.first + i] : T(0);
     __syncthreads();
     const T *Lp = L + d.l_off;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ T dblk[32][33];
     for (int jb = 0; jb < p; jb += 32) {
         const int kb = min(32, p - jb);
-        // stage the diagonal block with coalesced loads (column j contiguous)
+        if (threadIdx.x < 32 * NR) {
+            const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
+            xb[threadIdx.x] = j < kb ? v[jb + j + r * f] : T(0);
+        }
+        // stage the inverse block with coalesced loads (column j contiguous)
         for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-            int i = idx & 31, j = idx >> 5;
+            const int i = idx & 31, j = idx >> 5;
             dblk[i][j] = (i < kb && j < kb && i >= j) ? Lp[(jb + i) + (int64_t)(jb + j) * f] : T(0);
         }
         __syncthreads();
-        if (warp == 0) {
-            const T inv = lane < kb ? T(1) / dblk[lane][lane] : T(0);
+        const T *col0 = Lp + (int64_t)jb * f;
+        if (threadIdx.x < kb) {
+            // rows of B (warp 0, from shared memory): y_B = L[B,B]^{-1} x_B
+            const int li = threadIdx.x;
+            T acc[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                T val = lane < kb ? v[jb + lane + r * f] : T(0);
-                for (int j = 0; j < kb; ++j) {
-                    T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, inv, j);
-                    if (lane == j) val = yj;
-                    if (lane > j) val -= dblk[lane][j] * yj;
-                }
-                if (lane < kb) v[jb + lane + r * f] = val;
-            }
+            for (int r = 0; r < NR; ++r) acc[r] = T(0);
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] += dblk[li][j] * xb[j + 32 * r];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[jb + li + r * f] = acc[r];
         }
-        __syncthreads();
         if (kb == 32) {
-            // full block: issue the row's 32 loads before any arithmetic
-            const T *col0 = Lp + (int64_t)jb * f;
+            // full block: the row's 32 loads before any arithmetic
             for (int i = jb + 32 + threadIdx.x; i < f; i += blockDim.x) {
                 T l[32];
 #pragma unroll
@@ -546,8 +622,8 @@ __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, con
                     T a0 = T(0), a1 = T(0);
 #pragma unroll
                     for (int j = 0; j < 32; j += 2) {
-                        a0 += l[j] * v[jb + j + r * f];
-                        a1 += l[j + 1] * v[jb + j + 1 + r * f];
+                        a0 += l[j] * xb[j + 32 * r];
+                        a1 += l[j + 1] * xb[j + 1 + 32 * r];
                     }
                     v[i + r * f] -= a0 + a1;
                 }
@@ -558,9 +634,9 @@ __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, con
 #pragma unroll
                 for (int r = 0; r < NR; ++r) acc[r] = T(0);
                 for (int j = 0; j < kb; ++j) {
-                    T l = Lp[i + (int64_t)(jb + j) * f];
+                    const T l = col0[i + (int64_t)j * f];
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[r] += l * v[jb + j + r * f];
+                    for (int r = 0; r < NR; ++r) acc[r] += l * xb[j + 32 * r];
                 }
 #pragma unroll
                 for (int r = 0; r < NR; ++r) v[i + r * f] -= acc[r];
@@ -577,40 +653,45 @@ __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, con
     }
 }
 
-// Backward substitution: x_p = L11^{-T} (x_p - L21^T x_s).
+// Backward substitution for the fronts of one level, one CTA per front: for
+// each block B of 32 pivots from the last to the first,
+//   x_B = L[B,B]^{-T} y_B - W[i,B]^T x_i   (rows i below B),
+// one reduction down each column of the block over the rows from B to the end
+// of the front (the rows of B with +, the rows below with -); warp w owns the
+// columns w, w + 8, ..., its lanes stride the rows with 8 loads in flight, and
+// a shuffle tree adds the lanes.  No serial triangular solve remains.
 template <class T, int NR>
 __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
                                              const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
                                              int kcols, int c0) {
     extern __shared__ unsigned char smraw[];
-    T *v = reinterpret_cast<T *>(smraw);
-    __shared__ T red[32][NR];
     const FrontDesc d = D[fronts[blockIdx.x]];
     const int p = d.p, f = d.p + d.q, n = d.vlen;
+    T *v = reinterpret_cast<T *>(smraw);
+    T *red = v + (int64_t)f * NR;   // 32 x NR column results of the block
     T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
     for (int i = threadIdx.x; i < f; i += blockDim.x)
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             v[i + r * f] = i < p ? xs[(int64_t)r * n + d.first + i] : xs[(int64_t)r * n + rows[d.row_off + i]];
     __syncthreads();
+    if (p == 0) return;
     const T *Lp = L + d.l_off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (p == 0) return;
-    __shared__ T dblk[32][33];
     for (int jb = ((p - 1) / 32) * 32; jb >= 0; jb -= 32) {
         const int kb = min(32, p - jb);
-        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-            int i = idx & 31, j = idx >> 5;
-            dblk[i][j] = (i < kb && j < kb && i >= j) ? Lp[(jb + i) + (int64_t)(jb + j) * f] : T(0);
-        }
-        // red[j] = sum_{i >= jb+kb} L[i][jb+j] v[i]; warp w owns columns j = w, w+nw, ...
         for (int j = warp; j < kb; j += nw) {
-            T acc[NR];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] = T(0);
             const T *col = Lp + (int64_t)(jb + j) * f;
+            T acc[NR];
+            {
+                // rows of B: L[B,B]^{-1}[i, j] y_i for i >= j, negated here and restored below
+                const bool in = lane >= j && lane < kb;
+                const T l = in ? col[jb + lane] : T(0);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = -(l * v[jb + (in ? lane : 0) + r * f]);
+            }
             int i = jb + kb + lane;
-            // 8 independent loads per lane in flight
+            // rows below B: + W[i, j] x_i, 8 independent loads per lane in flight
             for (; i + 7 * 32 < f; i += 8 * 32) {
                 T l[8];
 #pragma unroll
@@ -621,7 +702,7 @@ __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, con
                     for (int r = 0; r < NR; ++r) acc[r] += l[t] * v[i + 32 * t + r * f];
             }
             for (; i < f; i += 32) {
-                T l = col[i];
+                const T l = col[i];
 #pragma unroll
                 for (int r = 0; r < NR; ++r) acc[r] += l * v[i + r * f];
             }
@@ -630,22 +711,13 @@ __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, con
                 T a = acc[r];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (lane == 0) red[j][r] = a;
+                if (lane == 0) red[j + 32 * r] = -a;
             }
         }
         __syncthreads();
-        if (warp == 0) {
-            const T inv = lane < kb ? T(1) / dblk[lane][lane] : T(0);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                T val = lane < kb ? v[jb + lane + r * f] - red[lane][r] : T(0);
-                for (int j = kb - 1; j >= 0; --j) {
-                    T yj = __shfl_sync(0xffffffffu, val, j) * __shfl_sync(0xffffffffu, inv, j);
-                    if (lane == j) val = yj;
-                    if (lane < j) val -= dblk[j][lane] * yj;
-                }
-                if (lane < kb) v[jb + lane + r * f] = val;
-            }
+        if (threadIdx.x < 32 * NR) {
+            const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
+            if (j < kb) v[jb + j + r * f] = red[j + 32 * r];
         }
         __syncthreads();
     }
@@ -654,28 +726,69 @@ __global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, con
         for (int r = 0; r < NR; ++r) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
 }
 
+// Shared memory of the sweeps: static tiles plus the dynamic front vector and
+// staging area.  The dynamic limit is raised per kernel to the largest front
+// seen; build_plan calls sweep_smem_for_plan for every variant, so no
+// attribute is ever changed while a stream is being captured.
+constexpr size_t SMEM_PER_CTA = 227 * 1024;
+
 template <class T, int NR>
-static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c0, cudaStream_t s) {
-    // raise the dynamic shared-memory limit only when a larger front needs it
-    // (never inside a stream capture once the largest plan has been seen)
-    size_t smem = (size_t)P.max_f * NR * sizeof(T);
-    static size_t attr_set = 48 * 1024;
+static size_t sweep_static_smem() {
+    static size_t v = 0;
+    if (!v) {
+        cudaFuncAttributes a{}, b{};
+        GL_CUDA(cudaFuncGetAttributes(&a, k_fwd<T, NR>));
+        GL_CUDA(cudaFuncGetAttributes(&b, k_bwd<T, NR>));
+        v = std::max<size_t>(1, std::max(a.sharedSizeBytes, b.sharedSizeBytes));
+    }
+    return v;
+}
+
+template <class T, int NR>
+static size_t sweep_dyn_smem(int max_f) {
+    return ((size_t)std::max(max_f, 1) + 32) * NR * sizeof(T);
+}
+
+template <class T, int NR>
+static bool sweep_fits(int max_f) {
+    return sweep_dyn_smem<T, NR>(max_f) + sweep_static_smem<T, NR>() <= SMEM_PER_CTA;
+}
+
+template <class T, int NR>
+static void ensure_sweep_smem(int max_f) {
+    static size_t attr_set = 0;
+    if (!sweep_fits<T, NR>(max_f)) return;
+    const size_t smem = sweep_dyn_smem<T, NR>(max_f);
     if (smem > attr_set) {
         GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set = smem;
     }
+}
+
+void sweep_smem_for_plan(int max_f) {
+    ensure_sweep_smem<double, 1>(max_f);
+    ensure_sweep_smem<double, 2>(max_f);
+    ensure_sweep_smem<double, 4>(max_f);
+    ensure_sweep_smem<float, 1>(max_f);
+    ensure_sweep_smem<float, 2>(max_f);
+    ensure_sweep_smem<float, 4>(max_f);
+}
+
+template <class T, int NR>
+static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c0, cudaStream_t s) {
+    ensure_sweep_smem<T, NR>(P.max_f);
     const int nlev = (int)P.levels.size();
     for (int dpt = nlev - 1; dpt >= 0; --dpt) {
         const Level &Lv = P.levels[dpt];
         if (Lv.fronts.empty()) continue;
-        size_t sm = (size_t)Lv.max_f * NR * sizeof(T);
+        const size_t sm = sweep_dyn_smem<T, NR>(Lv.max_f);
         k_fwd<T, NR><<<(unsigned)Lv.fronts.size(), 256, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
     }
     for (int dpt = 0; dpt < nlev; ++dpt) {
         const Level &Lv = P.levels[dpt];
         if (Lv.fronts.empty()) continue;
-        size_t sm = (size_t)Lv.max_f * NR * sizeof(T);
+        const size_t sm = sweep_dyn_smem<T, NR>(Lv.max_f);
         k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), 256, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
     }
     GL_CUDA(cudaGetLastError());
@@ -683,8 +796,8 @@ static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c
 
 template <class T>
 void factor_solve(const FactorPlan &P, const T *L, T *x, int kcols, cudaStream_t s) {
-    int nr = (size_t)P.max_f * 4 * sizeof(T) <= 200 * 1024 ? 4 : ((size_t)P.max_f * 2 * sizeof(T) <= 200 * 1024 ? 2 : 1);
-    if ((size_t)P.max_f * sizeof(T) > 200 * 1024) fail(GL_ERR_INVALID_ARG, "factor_solve: front too large");
+    const int nr = sweep_fits<T, 4>(P.max_f) ? 4 : (sweep_fits<T, 2>(P.max_f) ? 2 : 1);
+    if (!sweep_fits<T, 1>(P.max_f)) fail(GL_ERR_INVALID_ARG, "factor_solve: front too large for shared memory");
     int c0 = 0;
     while (c0 < kcols) {
         int left = kcols - c0;

@@ -34,6 +34,7 @@ struct FactorPlan {
     std::vector<FrontDesc> fr;
     std::vector<Level> levels;               // index = depth
     int64_t l_size = 0;
+    int64_t nnz = 0;                         // lower-triangle entries: sum p(p+1)/2 + p q
     int64_t ws_max = 0;
     int max_f = 0;
     // device

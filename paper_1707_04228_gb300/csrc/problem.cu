@@ -245,20 +245,35 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
         BV.zero(s);
         local_K_apply(PG, E, P.C, P.geo, xg, V.p, BV.p, k, s);            // BV = Xi A^N Xi V
         std::vector<double> mu_prev((size_t)ng * k, 0.0), mu_now((size_t)ng * k);
+        // optional per-step timing of the iteration (GL_VERBOSE)
+        const bool timed = std::getenv("GL_VERBOSE") != nullptr;
+        cudaEvent_t ev[6] = {};
+        double step_ms[5] = {0, 0, 0, 0, 0};
+        if (timed)
+            for (auto &e : ev) GL_CUDA(cudaEventCreate(&e));
+        auto mark = [&](int i) {
+            if (timed) GL_CUDA(cudaEventRecord(ev[i], s));
+        };
         int it = 0;
         for (; it < iters; ++it) {
             // W = M^{-1} B V
+            mark(0);
             GL_CUDA(cudaMemcpyAsync(tmp.p, BV.p, sizeof(double) * gl * k, cudaMemcpyDeviceToDevice, s));
             factor_solve<double>(PG, LN.p, tmp.p, k, s);
             std::swap(V.p, tmp.p);
+            mark(1);
             BW.zero(s);
             local_K_apply(PG, E, P.C, P.geo, xg, V.p, BW.p, k, s);         // BW = B W
+            mark(2);
             local_gram(PG, V.p, BV.p, k, GM.p, s);                          // W^T M W = W^T (B V)
             local_gram(PG, V.p, BW.p, k, GB.p, s);                          // W^T B W
+            mark(3);
             small_geneig(ng, k, GB.p, GM.p, Y.p, mu.p, P.d_err, s);
             check_err(P, "GenEO Rayleigh-Ritz");
+            mark(4);
             local_rotate(PG, V.p, Y.p, k, tmp.p, s);
             local_rotate(PG, BW.p, Y.p, k, tmp.p, s);
+            mark(5);
             std::swap(BV.p, BW.p);
             GL_CUDA(cudaMemcpyAsync(mu_now.data(), mu.p, mu_now.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
             GL_CUDA(cudaStreamSynchronize(s));
@@ -269,6 +284,12 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
                     change = std::max(change, std::fabs(now - prev) / std::fabs(now));
                 }
             mu_prev = mu_now;
+            if (timed)
+                for (int q = 0; q < 5; ++q) {
+                    float ms = 0.f;
+                    GL_CUDA(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
+                    step_ms[q] += ms;
+                }
             // Ritz values settle like rate^(2 it); 1e-12 leaves the Ritz vectors accurate to
             // about 1e-6, far below what changes the coarse space's effect on PCG.
             if (it >= 4 && change < 1e-12) {
@@ -286,7 +307,14 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
             }
             std::fprintf(stderr, "[gl]   group %d-%d: %d iterations, lambda_nev in [%.3g, %.3g], worst rate %.3f\n", j0,
                          j1 - 1, it, lo, hi, worst);
+            const double nit = std::max(it, 1);
+            std::fprintf(stderr,
+                         "[gl]     per iteration: solve %.1f ms, local K %.1f ms, Gram %.1f ms, Rayleigh-Ritz %.1f ms, "
+                         "rotate %.1f ms (k = %d)\n",
+                         step_ms[0] / nit, step_ms[1] / nit, step_ms[2] / nit, step_ms[3] / nit, step_ms[4] / nit, k);
         }
+        if (timed)
+            for (auto &e : ev) cudaEventDestroy(e);
         max_its = std::max(max_its, it);
         for (int j = 0; j < ng; ++j)
             for (int a = 0; a < nev; ++a) out.eig[(size_t)(j0 + j) * nev + a] = 1.0 / mu_now[(size_t)j * k + a] - sigma;

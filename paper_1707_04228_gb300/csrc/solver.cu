@@ -329,6 +329,21 @@ void setup(gl_ctx *c, const gl_opts &o) {
         build_plan(syms, c->PD, s);
     }
     stamp(c, "Dirichlet symbolic");
+    if (std::getenv("GL_VERBOSE")) {
+        // per dissection level: fronts, factor nonzeros the sweeps touch, the largest front
+        for (size_t dpt = 0; dpt < c->PD.levels.size(); ++dpt) {
+            const Level &Lv = c->PD.levels[dpt];
+            double ent = 0, emax = 0;
+            for (int g : Lv.fronts) {
+                const FrontDesc &d = c->PD.fr[g];
+                const double e = 0.5 * d.p * (d.p + 1.0) + (double)d.p * d.q;
+                ent += e;
+                emax = std::max(emax, e);
+            }
+            std::fprintf(stderr, "[gl]   level %2zu: %7zu fronts, %9.3e entries, largest %9.3e, max_f %d\n", dpt,
+                         Lv.fronts.size(), ent, emax, Lv.max_f);
+        }
+    }
     if (c->opts.precision == GL_PREC_MIXED) {
         c->LD64.release();
         c->LD32.alloc(c->PD.l_size);
@@ -1312,6 +1327,7 @@ int gl_profile_read(gl_ctx *c, gl_profile_data *out) {
         out->n_local = c->prof.count[PH_LOCAL];
         out->n_coarse = c->prof.count[PH_COARSE];
         out->factor_entries = c->PD.l_size;
+        out->factor_nonzeros = c->PD.nnz;
         out->local_dofs = c->PD.n_local;
         out->factor_bytes_per_entry = c->opts.precision == GL_PREC_MIXED ? 4 : 8;
         out->n_elem = c->m.n_elem;

@@ -181,6 +181,48 @@ def flat_plate_c0() -> Laminate:
     return lam
 
 
+def centre_arc_length(lam: Laminate):
+    """Element-centre coordinate along the laminate (nx,): the arc length of the
+    mid-thickness surface (curved; limbs included) or x (flat), in mm."""
+    tc = 0.5 * (lam.sv[:-1] + lam.sv[1:])
+    if lam.geometry != 1:
+        return tc
+    rmid = lam.R_inner + 0.5 * lam.thickness
+    arc = math.radians(lam.arc_deg)
+    return np.where(tc < 0, tc * lam.limb_L,
+                    np.where(tc <= 1, tc * arc * rmid, arc * rmid + (tc - 1) * lam.limb_L))
+
+
+def resin_elements(lam: Laminate):
+    """Boolean per element (element order x fastest, then y, then z): isotropic resin layer."""
+    iso = np.array([lam.materials[m]["kind"] == "iso" for m in lam.layer_mat])
+    ez = iso[lam.elem_layer()]
+    return np.broadcast_to(ez[:, None, None], (lam.nz, lam.ny, lam.nx)).reshape(-1).copy()
+
+
+def arc_resin_mask(lam: Laminate):
+    """Resin elements of the arc (centre parameter 0 < t < 1): the corner region whose
+    through-thickness stress the adjoint objective aggregates."""
+    tc = 0.5 * (lam.sv[:-1] + lam.sv[1:])
+    arc = (tc > 0) & (tc < 1)
+    return resin_elements(lam) & np.broadcast_to(arc[None, None, :], (lam.nz, lam.ny, lam.nx)).reshape(-1)
+
+
+def wrinkle_patch_mask(lam: Laminate, size_s=10.0, size_l=10.0):
+    """Ply (non-resin) elements whose centres lie in a size_s x size_l mm patch of
+    the (s, l) surface centred mid-arc (mid-length when flat) and mid-width:
+    the misalignment parameters of the adjoint study."""
+    s = centre_arc_length(lam)
+    if lam.geometry == 1:
+        s0 = 0.5 * math.radians(lam.arc_deg) * (lam.R_inner + 0.5 * lam.thickness)
+    else:
+        s0 = 0.5 * (s[0] + s[-1])
+    lc = 0.5 * (lam.lv[:-1] + lam.lv[1:])
+    l0 = 0.5 * (lam.lv[0] + lam.lv[-1])
+    ins = (np.abs(lc - l0)[:, None] <= 0.5 * size_l) & (np.abs(s - s0)[None, :] <= 0.5 * size_s)
+    return ~resin_elements(lam) & np.broadcast_to(ins[None], (lam.nz, lam.ny, lam.nx)).reshape(-1)
+
+
 def gaussian_theta(lam: Laminate, amp_deg, width_mm, s_centre=None, r_sigma=None,
                    l_centre=None, l_sigma=None):
     """Per-element misalignment theta(s, r) = A exp(-(s-s0)^2/2w^2) exp(-(r-r0)^2/2 sr^2).

@@ -60,7 +60,7 @@ class gl_profile_data(C.Structure):
                 ("n_ku", C.c_int64), ("n_local", C.c_int64), ("n_coarse", C.c_int64),
                 ("factor_entries", C.c_int64), ("local_dofs", C.c_int64), ("factor_bytes_per_entry", C.c_int),
                 ("factor_levels", C.c_int), ("n_elem", C.c_int64), ("n_dof", C.c_int64), ("n_sub", C.c_int),
-                ("n_coarse_dim", C.c_int)]
+                ("n_coarse_dim", C.c_int), ("factor_nonzeros", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -245,7 +245,8 @@ class Solver:
         rc = self.lib.gl_solve(self.ctx, _ptr(f), _ptr(out), C.byref(info))
         if check:
             _check(self.lib, rc)
-        return out, info.as_dict()
+        self.last_info = info.as_dict()
+        return out, self.last_info
 
     def stress(self, u, s33=None, t13=None):
         ne = self.n_elem
@@ -299,7 +300,8 @@ class Solver:
         grad = np.empty(self.n_elem) if grad is None else grad
         info = gl_info()
         _check(self.lib, self.lib.gl_adjoint(self.ctx, _ptr(u), _ptr(dJdu), _ptr(grad), C.byref(info)))
-        return grad, info.as_dict()
+        self.last_adjoint_info = info.as_dict()
+        return grad, self.last_adjoint_info
 
     def profile(self, enable=True):
         _check(self.lib, self.lib.gl_profile(self.ctx, 1 if enable else 0))

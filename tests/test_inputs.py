@@ -1,0 +1,34 @@
+"""Input-description helpers (no GPU): the element masks that select the adjoint
+objective's region and the misalignment patch agree with the oracle's own mesh
+classification and with the stated geometry."""
+import math
+
+import numpy as np
+
+from oracle import fem
+from paper_1707_04228_gb300 import inputs
+
+
+def test_resin_and_arc_masks_match_the_oracle_mesh():
+    lam = inputs.corner_mini(n_arc=8, n_limb=2, n_width=6, nel_layer=2, angles=(0, 90), nsub=(4, 2, 1), nev=8,
+                             width=6.0, wrinkle_w=1.0)
+    mesh = fem.Mesh(lam)
+    assert np.array_equal(inputs.resin_elements(lam), mesh.is_resin)
+    tc = 0.5 * (lam.sv[mesh.eijk[:, 0]] + lam.sv[mesh.eijk[:, 0] + 1])
+    assert np.array_equal(inputs.arc_resin_mask(lam), mesh.is_resin & (tc > 0) & (tc < 1))
+
+
+def test_patch_mask_geometry_on_the_corner():
+    lam = inputs.corner_c1()
+    m = inputs.wrinkle_patch_mask(lam, 10.0, 10.0).reshape(lam.nz, lam.ny, lam.nx)
+    s = inputs.centre_arc_length(lam)
+    rmid = lam.R_inner + 0.5 * lam.thickness
+    s0 = 0.5 * math.radians(lam.arc_deg) * rmid
+    cols = np.flatnonzero(m.any(axis=(0, 1)))
+    assert np.all(np.abs(s[cols] - s0) <= 5.0)
+    lc = 0.5 * (lam.lv[:-1] + lam.lv[1:])
+    rows = np.flatnonzero(m.any(axis=(0, 2)))
+    assert np.all(np.abs(lc[rows] - 7.5) <= 5.0) and len(rows) == 20
+    assert not np.any(m & inputs.resin_elements(lam).reshape(m.shape))
+    # arc length is continuous across the limb/arc joints and grows monotonically
+    assert np.all(np.diff(s) > 0)
