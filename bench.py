@@ -296,6 +296,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count", type=int, default=96, help="laminates in --config batch")
     ap.add_argument("--fd", type=int, default=0, help="central-difference checks in --config adjoint")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="after a mixed-precision run, solve the same laminate in FP64 and report the differences")
     args = ap.parse_args()
     rank, local_rank, world = dist_env()
     if args.config == "batch" and args.impl == "ours":
@@ -417,6 +419,25 @@ def main():
           "fp64_frac": ku_flops / (ku_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "ms": ku_ms,
           "bytes_per_launch": ku_bytes, "flops_per_launch": ku_flops}
 
+    # mixed precision against the plain FP64 form on the same laminate (after the timing)
+    vs_fp64 = None
+    if args.compare_fp64 and prec == 1:
+        _, peak_m = s.stress(u, s33, t13)[::2]
+        u_m = u.cpu().numpy()
+        it_m = info["iters"]
+        s.close()
+        t2 = time.perf_counter()
+        s64 = lib.Solver.from_laminate(lam, device=local_rank, precision=0, tol=1e-10, max_iter=5000)
+        setup64 = time.perf_counter() - t2
+        _, info64 = s64.solve(f, out=u)
+        _, peak64 = s64.stress(u, s33, t13)[::2]
+        u64 = u.cpu().numpy()
+        vs_fp64 = {"rel_l2_u": float(np.linalg.norm(u_m - u64) / np.linalg.norm(u64)),
+                   "rel_peak_s33": float(abs(peak_m - peak64) / abs(peak64)),
+                   "iters_mixed": it_m, "iters_fp64_1e-10": info64["iters"], "setup_fp64_s": setup64,
+                   "rel_resid_true_fp64": info64["rel_resid_true"]}
+        s64.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = run_oracle(3, 1, max_seconds=40)
@@ -434,6 +455,8 @@ def main():
                 "clocks": clk.summary(), "gpu_launches": launches, "setup_s": setup_s,
                 "iters_per_solve": iters / max(args.steps, 1), "rel_resid_true": info["rel_resid_true"],
                 "n_free": info["n_free"], "factor_nonzeros": fe, "n_coarse": info["n_coarse"]}
+        if vs_fp64 is not None:
+            line["vs_fp64"] = vs_fp64
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -222,6 +222,29 @@ def test_pure_bending_exact_quadratic():
     assert np.linalg.norm(u - ex) <= 1e-10 * np.linalg.norm(ex)
 
 
+def test_tip_loaded_cantilever_approaches_timoshenko():
+    """A clamped isotropic beam (L/h = 20) under a tip shear load: the 3D Q2
+    solution approaches Timoshenko's P L^3/(3EI) + P L/(kGA), k = 5/6, within
+    about 1% (the clamp's 3D constraint accounts for the rest) and settles
+    under mesh refinement.  Convergence only, not an exact solution."""
+    E, nu = 10000.0, 0.3
+    G = E / (2 * (1 + nu))
+    iso = dict(kind="iso", E=E, nu=nu)
+    L, h, b, tau = 20.0, 1.0, 1.0, 0.01
+    P, I, A = tau * b * h, b * h ** 3 / 12, b * h
+    w_timo = P * L ** 3 / (3 * E * I) + P * L / (5 / 6 * G * A)
+    tips = []
+    for nx in (20, 40):
+        lam = block(nx, 1, [(2, h, 0, 0.0)], sx=L, sy=b, mats=[iso])
+        lam.traction = [(1, (0.0, 0.0, tau))]
+        lam.dir_dof, lam.dir_val = inputs.clamp_face(lam, 0)
+        mesh = fem.Mesh(lam)
+        u = fem.System(mesh).direct().reshape(-1, 3)
+        tips.append(u[np.isclose(mesh.X[:, 0], L), 2].mean())
+    assert abs(tips[0] / w_timo - 1.0) <= 0.01 and abs(tips[1] / w_timo - 1.0) <= 0.01
+    assert abs(tips[1] / tips[0] - 1.0) <= 0.005
+
+
 def test_clt_laminate_in_plane_strain_exact():
     """[0/R/90/R/90/R/0] under in-plane strain: per-layer plane stress, reproduced exactly.
 
@@ -455,6 +478,30 @@ def test_oracle_adjoint_gradient_matches_central_differences():
         fd = (adjoint.objective_at(lam, tp, mask, 8) - adjoint.objective_at(lam, tm, mask, 8)) / (2 * h)
         assert abs(fd - grad[e]) <= 1e-6 * np.abs(grad).max()
     assert np.all(grad[mesh.is_resin & ~mask] == 0.0)
+
+
+def test_oracle_adjoint_step_sweep_shows_second_order_differences():
+    """Central differences of J against the oracle's adjoint gradient over
+    h = 1e-2 .. 1e-6 rad: the error falls as h^2 (a factor ~100 per decade)
+    until rounding takes over, where it stays below 1e-6 relative."""
+    from oracle import adjoint
+    lam = inputs.corner_mini(n_arc=4, n_limb=1, n_width=2, nel_layer=1, angles=(0, 90), limb_L=2.0, width=2.0)
+    mesh = fem.Mesh(lam)
+    mask = inputs.arc_resin_mask(lam)
+    J, grad, u = adjoint.gradient(fem.System(mesh), mask, 8)
+    theta0 = mesh.theta.copy()
+    plies = np.nonzero(~mesh.is_resin)[0]
+    e = plies[np.argmax(np.abs(grad[plies]))]
+    err = []
+    for h in (1e-2, 1e-3, 1e-4, 1e-6):
+        tp, tm = theta0.copy(), theta0.copy()
+        tp[e] += h
+        tm[e] -= h
+        fd = (adjoint.objective_at(lam, tp, mask, 8) - adjoint.objective_at(lam, tm, mask, 8)) / (2 * h)
+        err.append(abs(fd - grad[e]) / abs(grad[e]))
+    assert 70.0 <= err[0] / err[1] <= 130.0
+    assert err[1] / err[2] >= 40.0
+    assert err[3] <= 1e-6
 
 
 def test_failure_index_uniform_stress_closed_form():
