@@ -15,6 +15,13 @@ device-resident load vector, followed by the stress recovery; the setup
 (geometry, factorisations, GenEO coarse space) runs once before the warm-up
 and is reported as setup_s.  value = free DOFs x PCG iterations / solve time.
 
+Other configurations (--config): corner_small (a 32x8x23 dry-run case),
+corner_wide / corner_mixed (the 120x45x92 corner, 12,171,705 DOF, in FP64 or
+with FP32 local factors; --compare-fp64 adds the FP64 solve of the same
+laminate and reports the differences), batch (96 flat laminates solved
+together, autotuned decompositions) and adjoint (the gradient of the resin
+stress p-norm with respect to every element's misalignment angle).
+
 --impl reference times the CPU oracle (oracle/), as it stands, on a bounded
 sample of the same laminate family on the host cores.
 """

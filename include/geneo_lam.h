@@ -77,6 +77,13 @@ typedef struct {
  *            the laminate normal.
  *   theta_e  per-element fibre misalignment angle (rad, rotation about the
  *            width axis l), length nx*ny*nz, or NULL for zero.
+ *   node_dr  per-node offset (mm) added to the through-thickness coordinate
+ *            (depth r from the inner face, or z when flat) before the curved
+ *            map: a geometric wrinkle r^ = r + f(s, l, r) as in Section 3
+ *            (Eq. eq-wrinkle); length (2nx+1)(2ny+1)(2nz+1) in node order (x
+ *            fastest, then y, then z), or NULL.  The offset nodes must keep
+ *            every through-thickness node column strictly increasing, else
+ *            gl_set_mesh returns GL_ERR_INVALID_ARG.
  * Material axes: R = R_l(psi + theta_e) R_r(phi), psi the frame angle at the
  * element centre (0 on limb 1 and flat plates), C_e constant per element. */
 typedef struct {
@@ -90,6 +97,7 @@ typedef struct {
     int geometry;              /* 0 flat, 1 curved */
     double R_inner, limb_L, arc_deg;
     const double *theta_e;
+    const double *node_dr;
 } gl_mesh;
 
 /* Solver options.

@@ -225,6 +225,10 @@ class Mesh:
         ln = q2_node_params(lam.lv)
         rn = q2_node_params(rv_vertices(lam))
         T, Lg, R = np.meshgrid(tn, ln, rn, indexing="ij")      # (NX, NY, NZ)
+        dr = getattr(lam, "node_dr", None)
+        if dr is not None:
+            # geometric wrinkle (Section 3, Eq. eq-wrinkle): r^ = r + f, before the map
+            R = R + np.asarray(dr).reshape(self.NZ, self.NY, self.NX).transpose(2, 1, 0)
         X = map_point(lam, T, Lg, R)
         # node n = ix + NX*(iy + NY*iz)
         self.X = X.transpose(2, 1, 0, 3).reshape(-1, 3)

@@ -13,7 +13,10 @@
 //      diagonal block (POTRF), panel below (TRSM), trailing lower triangle
 //      (SYRK/GEMM) -- the trailing update also forms the update matrix;
 //   5. copy the f x p panel into the factor array.
-// The solves walk the same levels: forward (leaves to root) and backward.
+// After all levels the stored factor is put in partitioned-inverse form
+// (k_block_inverse: inverted 32x32 diagonal blocks, rows below multiplied by
+// them).  The solves walk the same levels: forward (leaves to root) and
+// backward, each block step a plain product with that form.
 #include <algorithm>
 #include <cstdio>
 

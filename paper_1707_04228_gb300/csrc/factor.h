@@ -51,12 +51,15 @@ void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_
 // Numeric factorisation.  Front entries from the element matrices, formed on
 // the fly in FP64 from C_e (36 per element) and the Gauss-point geometry (270
 // per element), scaled by (1 + sigma xi_i xi_j) (xi indexed by local DOF, may
-// be NULL when sigma == 0).  Factor values of type T.
+// be NULL when sigma == 0).  Factor values of type T, left in the
+// partitioned-inverse form that factor_solve reads (every 32-pivot diagonal
+// block inverted, the rows below it multiplied by that inverse).
 template <class T>
 void numeric_factor(FactorPlan &P, const double *C, const double *geo, const double *xi, double sigma, T *L, int *d_err,
                     cudaStream_t s);
 
-// x <- L^{-T} L^{-1} x for local multi-vectors of kcols columns per subdomain,
+// x <- L^{-T} L^{-1} x (L as factored; stored in partitioned-inverse form)
+// for local multi-vectors of kcols columns per subdomain,
 // each column of the subdomain's length stored contiguously:
 // x[vec_off*kcols + c*n + i] (kcols = 1: plain concatenated local vectors).
 template <class T>

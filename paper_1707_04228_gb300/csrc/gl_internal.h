@@ -99,6 +99,7 @@ struct MeshHost {
     std::vector<int> layer_mat;
     std::vector<double> layer_angle;         // rad
     std::vector<double> theta;               // per element (rad), may be empty
+    std::vector<double> node_dr;             // per node through-thickness offset (mm), may be empty
 };
 
 // ---------------------------------------------------------------- decomposition / symbolic
@@ -140,7 +141,7 @@ void build_symbolic(const MeshHost &m, const SubBox &b, const std::vector<uint8_
 
 // ---------------------------------------------------------------- kernels (launchers)
 void launch_node_coords(const MeshHost &m, const double *tn, const double *ln, const double *rn,
-                        double *X, cudaStream_t s);
+                        const double *dr, double *X, cudaStream_t s);
 void launch_elem_material(int64_t n_elem, int nx, int ny, const int *layer_of_ez, const int *layer_mat,
                           const double *layer_angle, const double *theta, const double *psi,
                           const double *matC, double *C, cudaStream_t s);

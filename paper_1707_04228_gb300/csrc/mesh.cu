@@ -13,16 +13,19 @@ namespace gl {
 
 // ---------------------------------------------------------------- node coordinates
 
+// dr (may be NULL): per-node offset of the through-thickness coordinate, the
+// geometric wrinkle r^ = r + f(s, l, r) of Section 3, applied before the map.
 __global__ void k_node_coords(int NX, int NY, int NZ, int geometry, double R_inner, double L,
                               double arc, const double *__restrict__ tn, const double *__restrict__ ln,
-                              const double *__restrict__ rn, double *__restrict__ X) {
+                              const double *__restrict__ rn, const double *__restrict__ dr,
+                              double *__restrict__ X) {
     int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t total = (int64_t)NX * NY * NZ;
     if (n >= total) return;
     int ix = (int)(n % NX);
     int iy = (int)((n / NX) % NY);
     int iz = (int)(n / ((int64_t)NX * NY));
-    double t = tn[ix], l = ln[iy], d = rn[iz];
+    double t = tn[ix], l = ln[iy], d = rn[iz] + (dr ? dr[n] : 0.0);
     double x, y = l, z;
     if (geometry == 0) {
         x = t;
@@ -41,10 +44,10 @@ __global__ void k_node_coords(int NX, int NY, int NZ, int geometry, double R_inn
 }
 
 void launch_node_coords(const MeshHost &m, const double *tn, const double *ln, const double *rn,
-                        double *X, cudaStream_t s) {
+                        const double *dr, double *X, cudaStream_t s) {
     int64_t n = m.n_nodes;
     k_node_coords<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.NX, m.NY, m.NZ, m.geometry, m.R_inner,
-                                                             m.limb_L, m.arc_rad, tn, ln, rn, X);
+                                                             m.limb_L, m.arc_rad, tn, ln, rn, dr, X);
     GL_CUDA(cudaGetLastError());
 }
 

@@ -88,7 +88,7 @@ struct gl_ctx {
     MeshHost m;
     std::vector<double> psi_x;
     // device mesh data
-    DBuf<double> d_tn, d_ln, d_rn, d_X, d_C, d_geo, d_psi, d_theta, d_layer_angle, d_matC;
+    DBuf<double> d_tn, d_ln, d_rn, d_dr, d_X, d_C, d_geo, d_psi, d_theta, d_layer_angle, d_matC;
     DBuf<int> d_layer_of_ez, d_layer_mat;
     DBuf<uint8_t> d_resin;
     // boundary data
@@ -185,7 +185,9 @@ void build_geometry(gl_ctx *c) {
     c->d_ln.upload(m.ln, s);
     c->d_rn.upload(m.rn, s);
     c->d_X.alloc(3 * m.n_nodes);
-    launch_node_coords(m, c->d_tn.p, c->d_ln.p, c->d_rn.p, c->d_X.p, s);
+    if (!m.node_dr.empty()) c->d_dr.upload(m.node_dr, s);
+    else c->d_dr.release();
+    launch_node_coords(m, c->d_tn.p, c->d_ln.p, c->d_rn.p, m.node_dr.empty() ? nullptr : c->d_dr.p, c->d_X.p, s);
     c->psi_x.assign(m.nx, 0.0);
     if (m.geometry == 1)
         for (int ex = 0; ex < m.nx; ++ex) {
@@ -1040,6 +1042,17 @@ int gl_set_mesh(gl_ctx *c, const gl_mesh *mesh) {
         m.ln = mid(m.lv);
         m.rn = mid(m.rv);
         if (mesh->theta_e) m.theta = fetch(mesh->theta_e, m.n_elem);
+        if (mesh->node_dr) {
+            m.node_dr = fetch(mesh->node_dr, m.n_nodes);
+            // every through-thickness node column must stay strictly increasing
+            for (int64_t col = 0; col < (int64_t)m.NX * m.NY; ++col)
+                for (int iz = 0; iz + 1 < m.NZ; ++iz) {
+                    const int64_t a = col + (int64_t)m.NX * m.NY * iz, b = a + (int64_t)m.NX * m.NY;
+                    GL_REQUIRE(std::isfinite(m.node_dr[a]) && std::isfinite(m.node_dr[b]) &&
+                                   m.rn[iz] + m.node_dr[a] < m.rn[iz + 1] + m.node_dr[b],
+                               "node_dr folds a through-thickness node column");
+                }
+        }
         c->m = std::move(m);
         c->have_mesh = true;
         c->ready = false;

@@ -56,6 +56,7 @@ class Laminate:
     limb_L: float = 0.0
     arc_deg: float = 90.0
     theta: np.ndarray | None = None   # (nz, ny, nx) misalignment, rad
+    node_dr: np.ndarray | None = None  # (NZ, NY, NX) through-thickness node offset (geometric wrinkle), mm
     dir_dof: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     dir_val: np.ndarray = field(default_factory=lambda: np.zeros(0))
     traction: list = field(default_factory=list)   # [(face, (tx, ty, tz))] MPa, global axes
@@ -221,6 +222,69 @@ def wrinkle_patch_mask(lam: Laminate, size_s=10.0, size_l=10.0):
     l0 = 0.5 * (lam.lv[0] + lam.lv[-1])
     ins = (np.abs(lc - l0)[:, None] <= 0.5 * size_l) & (np.abs(s - s0)[None, :] <= 0.5 * size_s)
     return ~resin_elements(lam) & np.broadcast_to(ins[None], (lam.nz, lam.ny, lam.nx)).reshape(-1)
+
+
+def _q2_params(v):
+    """Q2 node parameters of a vertex array: vertices and edge midpoints."""
+    v = np.asarray(v, dtype=np.float64)
+    out = np.empty(2 * len(v) - 1)
+    out[0::2] = v
+    out[1::2] = 0.5 * (v[:-1] + v[1:])
+    return out
+
+
+def sech2_wrinkle(lam: Laminate, d, b1=0.2, b2_inner=0.5, b2_outer=0.25, b3=0.5,
+                  s_def=None, l_def=None, r_def=None):
+    """The paper's geometric wrinkle (Section 3, Eqs. eq-wrinkle and eq-f):
+    the through-thickness coordinate of every node moves by
+
+        f = d sech^2(pi (s - s_def) / b1) sech^2(pi (r - r_def) / (T b2)) sech^2(pi (l - l_def) / (W b3)),
+
+    b2 = b2_inner below r_def and b2_outer above it.  Readings: s is the arc
+    parameter t on [0, 1] (the paper's s on [0, pi] divided by pi; for flat
+    plates x divided by the length), r the depth from the inner face with the
+    laminate thickness T as its scale (the printed "R b2"), W the width.  The
+    fibres follow the wrinkled surfaces: theta_e = -atan(df/ds) at the element
+    centre (s the arc length of the ply at that depth; R_l(theta) tilts e_s
+    towards -r for theta > 0).  Returns (node_dr (NZ, NY, NX), theta (nz, ny, nx));
+    defaults centre the defect mid-arc, mid-width and mid-thickness."""
+    T = lam.thickness
+    W = float(lam.lv[-1] - lam.lv[0])
+    sv = np.asarray(lam.sv, dtype=np.float64)
+    if lam.geometry == 1:
+        to_s = lambda t: t                                  # arc parameter
+    else:
+        S = float(sv[-1] - sv[0])
+        to_s = lambda t: (t - sv[0]) / S
+    s_def = 0.5 if s_def is None else s_def
+    l_def = 0.5 * (lam.lv[0] + lam.lv[-1]) if l_def is None else l_def
+    r_def = 0.5 * T if r_def is None else r_def
+
+    def f_and_slope(t, l, r):
+        a_s = math.pi * (to_s(t) - s_def) / b1
+        b2 = np.where(r - r_def < 0, b2_inner, b2_outer)
+        a_r = math.pi * (r - r_def) / (T * b2)
+        a_l = math.pi * (l - l_def) / (W * b3)
+        f = d / np.cosh(a_s) ** 2 / np.cosh(a_r) ** 2 / np.cosh(a_l) ** 2
+        dfdu = -2.0 * np.tanh(a_s) * f * math.pi / b1       # d f / d(normalised s)
+        if lam.geometry == 1:
+            rr = lam.R_inner + r
+            dsdt = np.where((t >= 0) & (t <= 1), rr * math.radians(lam.arc_deg), lam.limb_L)
+            dfds = dfdu / dsdt
+        else:
+            dfds = dfdu / S
+        return f, dfds
+
+    tn, ln, rn = _q2_params(sv), _q2_params(lam.lv), _q2_params(lam.rv())
+    Rg, Lg, Tg = np.meshgrid(rn, ln, tn, indexing="ij")   # (NZ, NY, NX)
+    dr, _ = f_and_slope(Tg, Lg, Rg)
+    tc = 0.5 * (sv[:-1] + sv[1:])
+    lc = 0.5 * (lam.lv[:-1] + lam.lv[1:])
+    rv = lam.rv()
+    rc = 0.5 * (rv[:-1] + rv[1:])
+    Rc, Lc, Tc = np.meshgrid(rc, lc, tc, indexing="ij")   # (nz, ny, nx)
+    _, slope = f_and_slope(Tc, Lc, Rc)
+    return dr, -np.arctan(slope)
 
 
 def gaussian_theta(lam: Laminate, amp_deg, width_mm, s_centre=None, r_sigma=None,

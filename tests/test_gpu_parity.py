@@ -217,3 +217,36 @@ def test_coincident_subdomains_drop_coarse_columns(lib_mod):
     assert info["status"] == 0
     assert 0 < info["n_coarse_dropped"] <= 12
     assert rel(u, u_ref) <= 1e-8
+
+
+def wrinkled_corner():
+    """Mini curved corner carrying the paper's sech^2 geometric wrinkle (Section 3,
+    Eq. eq-f) instead of a misalignment field: nodes moved through the thickness,
+    fibre angles following the deformed plies."""
+    lam = inputs.corner_mini(n_arc=6, n_limb=1, n_width=4, nel_layer=2, angles=(0, 90), nsub=(3, 2, 1), nev=8,
+                             limb_L=2.0, width=4.0)
+    lam.node_dr, lam.theta = inputs.sech2_wrinkle(lam, 0.05)
+    return lam
+
+
+def test_wrinkled_corner_matches_oracle(lib_mod):
+    lam = wrinkled_corner()
+    mesh = fem.Mesh(lam)
+    sysm = fem.System(mesh)
+    s = lib_mod.Solver.from_laminate(lam)
+    x = inputs.random_vector(mesh.n_dof, 17)
+    assert rel(s.apply_K(x), sysm.K @ x) <= 1e-12
+    u_ref = sysm.direct()
+    u, info = s.solve()
+    assert info["status"] == 0 and rel(u, u_ref) <= 1e-8
+    _, _, peak = s.stress(u)
+    r33, _ = fem.stress_slr(mesh, u_ref)
+    assert abs(peak - r33[mesh.is_resin].max()) <= 1e-6 * np.abs(r33).max()
+
+
+def test_folding_wrinkle_is_rejected(lib_mod):
+    lam = wrinkled_corner()
+    lam.node_dr, lam.theta = inputs.sech2_wrinkle(lam, 2.0)     # larger than the thickness allows
+    with pytest.raises(lib_mod.GLError) as e:
+        lib_mod.Solver.from_laminate(lam)
+    assert e.value.code == -1

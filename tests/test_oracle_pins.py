@@ -161,6 +161,47 @@ def test_patch_test_linear_field_exact(curved):
     assert np.linalg.norm(u - exact) <= 1e-11 * np.linalg.norm(exact)
 
 
+def test_patch_test_on_wrinkled_curved_mesh():
+    """The geometric wrinkle moves nodes inside the Q2 (isoparametric) space:
+    a linear field prescribed on the boundary is still reproduced inside."""
+    rng = np.random.default_rng(5)
+    lam = block(6, 3, [(2, 0.4, 1, 0.0), (2, 0.3, 1, 0.0)], sx=inputs.graded(6, -1.0, 2.0, 3.0),
+                sy=[0.0, 0.7, 1.4, 2.0], geometry=1, R_inner=2.0, limb_L=1.5, arc_deg=90.0)
+    lam.node_dr, _ = inputs.sech2_wrinkle(lam, 0.04)
+    A = rng.standard_normal((3, 3)) * 1e-3
+    b = rng.standard_normal(3) * 1e-3
+    mesh = fem.Mesh(lam)
+    plain = fem.Mesh(block(6, 3, [(2, 0.4, 1, 0.0), (2, 0.3, 1, 0.0)], sx=inputs.graded(6, -1.0, 2.0, 3.0),
+                           sy=[0.0, 0.7, 1.4, 2.0], geometry=1, R_inner=2.0, limb_L=1.5, arc_deg=90.0))
+    assert np.abs(mesh.X - plain.X).max() > 0.01           # the nodes did move
+    nodes = all_boundary_nodes(mesh)
+    mesh, u = _solve_with_exact_dirichlet(lam, lambda X: X @ A.T + b, nodes)
+    exact = (mesh.X @ A.T + b).ravel()
+    assert np.linalg.norm(u - exact) <= 1e-11 * np.linalg.norm(exact)
+
+
+def test_wrinkle_fibre_angle_follows_the_deformed_plies():
+    """On a flat plate the misalignment returned with the wrinkle equals minus the
+    slope of the deformed ply surfaces measured on the oracle mesh (central
+    differences of the element-centre node heights along x), and a zero
+    amplitude leaves the mesh unchanged."""
+    lam = block(40, 4, [(6, 1.2, 0, 0.0)], sx=8.0, sy=4.0)
+    lam.node_dr, theta = inputs.sech2_wrinkle(lam, 0.1, b1=0.3)
+    mesh = fem.Mesh(lam)
+    Z = mesh.X[:, 2].reshape(mesh.NZ, mesh.NY, mesh.NX)
+    X = mesh.X[:, 0].reshape(mesh.NZ, mesh.NY, mesh.NX)
+    # element centres are the odd nodes; their neighbours along x are the even nodes
+    zc = Z[1::2, 1::2, :]
+    slope = (zc[:, :, 2::2] - zc[:, :, 0:-1:2]) / (X[1::2, 1::2, 2::2] - X[1::2, 1::2, 0:-1:2])
+    assert np.abs(theta).max() > np.radians(2.0)
+    # central differences over one element length: O(h^2), about 1% here
+    assert np.abs(theta + np.arctan(slope)).max() <= 0.03 * np.abs(theta).max()
+    flat = fem.Mesh(block(40, 4, [(6, 1.2, 0, 0.0)], sx=8.0, sy=4.0))
+    lam0 = block(40, 4, [(6, 1.2, 0, 0.0)], sx=8.0, sy=4.0)
+    lam0.node_dr, th0 = inputs.sech2_wrinkle(lam0, 0.0)
+    assert np.array_equal(fem.Mesh(lam0).X, flat.X) and np.all(th0 == 0.0)
+
+
 def test_symmetry_and_rigid_body_null_space():
     lam = block(2, 2, [(1, 0.3, 0, 45.0), (1, 0.1, 1, 0.0)], sx=[-0.5, 0.3, 1.0], sy=1.0,
                 geometry=1, R_inner=1.0, limb_L=1.0)
