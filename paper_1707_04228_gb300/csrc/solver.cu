@@ -77,6 +77,26 @@ struct Prof {
 };
 }  // namespace
 
+// A second stream on which the coarse correction of the preconditioner runs
+// while the local sweeps run on the main one (both add into z atomically);
+// fork/join events order it against the main stream (also inside a graph
+// capture).  Created on first use with the owner's device current.
+struct SideStream {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    void ensure() {
+        if (st) return;
+        GL_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        GL_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        GL_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    }
+    ~SideStream() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
 struct gl_ctx {
     Prof prof;
     int device = 0;
@@ -114,6 +134,7 @@ struct gl_ctx {
     double *h_pin = nullptr;
     double ms_setup = 0;
     int64_t n_free = 0;
+    SideStream side;
 
     ~gl_ctx() {
         if (h_pin) cudaFreeHost(h_pin);
@@ -260,6 +281,17 @@ void apply_K(gl_ctx *c, const double *x, double *y) {
 void apply_prec(gl_ctx *c, const double *r, double *z) {
     cudaStream_t s = c->stream;
     GL_CUDA(cudaMemsetAsync(z, 0, c->m.n_dof * sizeof(double), s));
+    // the coarse correction overlaps the local sweeps (whose upper dissection
+    // levels leave SMs idle) unless the phases are being timed separately
+    const bool side = c->co.n0 > 0 && !c->prof.on;
+    if (side) {
+        c->side.ensure();
+        GL_CUDA(cudaEventRecord(c->side.fork, s));
+        GL_CUDA(cudaStreamWaitEvent(c->side.st, c->side.fork, 0));
+        coarse_apply(c->co, r, z, c->cvec.p, c->cvec2.p, c->side.st);
+        GL_CUDA(cudaEventRecord(c->side.join, c->side.st));
+        g_launches += 3;
+    }
     prof_begin(c, PH_LOCAL);
     if (c->opts.precision == GL_PREC_MIXED) {
         gather_local<float>(c->PD, r, c->xl32.p, s);
@@ -272,7 +304,9 @@ void apply_prec(gl_ctx *c, const double *r, double *z) {
     }
     prof_end(c, PH_LOCAL);
     g_launches += 2 + factor_solve_launches(c->PD);
-    if (c->co.n0 > 0) {
+    if (side) {
+        GL_CUDA(cudaStreamWaitEvent(s, c->side.join, 0));
+    } else if (c->co.n0 > 0) {
         prof_begin(c, PH_COARSE);
         coarse_apply(c->co, r, z, c->cvec.p, c->cvec2.p, s);
         prof_end(c, PH_COARSE);
@@ -537,6 +571,7 @@ struct gl_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     double ms_setup = 0;
+    SideStream side;
     ~gl_batch() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
@@ -619,6 +654,16 @@ __global__ void k_seg_init(SegScalars S, int n) {
 void batch_precond(gl_batch *b, const double *r, double *z) {
     cudaStream_t s = b->stream;
     GL_CUDA(cudaMemsetAsync(z, 0, b->N * sizeof(double), s));
+    // coarse correction on the side stream, overlapping the local sweeps
+    const bool side = b->co.n0 > 0;
+    if (side) {
+        b->side.ensure();
+        GL_CUDA(cudaEventRecord(b->side.fork, s));
+        GL_CUDA(cudaStreamWaitEvent(b->side.st, b->side.fork, 0));
+        coarse_apply(b->co, r, z, b->c1.p, b->c2.p, b->side.st);
+        GL_CUDA(cudaEventRecord(b->side.join, b->side.st));
+        g_launches += 3;
+    }
     if (b->opts.precision == GL_PREC_MIXED) {
         gather_local<float>(b->PD, r, b->xl32.p, s);
         factor_solve<float>(b->PD, b->LD32.p, b->xl32.p, 1, s);
@@ -629,10 +674,7 @@ void batch_precond(gl_batch *b, const double *r, double *z) {
         scatter_add_local<double>(b->PD, b->xl64.p, z, s);
     }
     g_launches += 2 + factor_solve_launches(b->PD);
-    if (b->co.n0 > 0) {
-        coarse_apply(b->co, r, z, b->c1.p, b->c2.p, s);
-        g_launches += 3;
-    }
+    if (side) GL_CUDA(cudaStreamWaitEvent(s, b->side.join, 0));
 }
 
 void batch_ku(gl_batch *b, const double *x, double *y) {
