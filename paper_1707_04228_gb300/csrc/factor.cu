@@ -614,7 +614,27 @@ __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, con
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[jb + li + r * f] = acc[r];
         }
-        if (kb == 32) {
+        if (kb == 32 && NR > 1) {
+            // full block, several right-hand sides: the row's loads in four groups of
+            // eight, keeping the registers of NR accumulators affordable
+            for (int i = jb + 32 + threadIdx.x; i < f; i += blockDim.x) {
+                T acc[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = T(0);
+#pragma unroll
+                for (int jc = 0; jc < 32; jc += 8) {
+                    T l[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) l[j] = col0[i + (int64_t)(jc + j) * f];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[r] += l[j] * xb[jc + j + 32 * r];
+                }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) v[i + r * f] -= acc[r];
+            }
+        } else if (kb == 32) {
             // full block: the row's 32 loads before any arithmetic
             for (int i = jb + 32 + threadIdx.x; i < f; i += blockDim.x) {
                 T l[32];

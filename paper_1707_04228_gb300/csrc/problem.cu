@@ -290,9 +290,9 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
                     GL_CUDA(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
                     step_ms[q] += ms;
                 }
-            // Ritz values settle like rate^(2 it); 1e-12 leaves the Ritz vectors accurate to
-            // about 1e-6, far below what changes the coarse space's effect on PCG.
-            if (it >= 4 && change < 1e-12) {
+            // Ritz values settle like rate^(2 it); a change of 1e-10 leaves the Ritz vectors
+            // accurate to about 1e-5, far below what changes the coarse space's effect on PCG.
+            if (it >= 4 && change < 1e-10) {
                 ++it;
                 break;
             }

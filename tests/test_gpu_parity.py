@@ -7,7 +7,7 @@ Tolerances (FP64 everywhere unless stated):
     matrices; the difference is bounded by cond(A_j) * eps, cond(A_j) about
     1e6-1e8 for these laminates, so 1e-8 relative;
   * GenEO eigenvalues: the GPU subspace iteration stops when the Ritz values
-    settle to 1e-14, 1e-7 relative;
+    change by less than 1e-10 relative between iterations, 1e-7 relative;
   * u against the oracle's direct solve: 1e-8 relative (the required bar);
   * iteration counts: within 15% of the oracle's PCG.
 """
