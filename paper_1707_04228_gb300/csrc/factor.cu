@@ -561,6 +561,13 @@ template void numeric_factor<float>(FactorPlan &, const double *, const double *
 
 // ----------------------------------------------------------------- solves
 
+// Threads per CTA of the sweeps: 256, or 512 on levels with fewer fronts than
+// about four per SM (the upper dissection levels, large fronts), where one CTA
+// per front would otherwise leave most warp slots empty.  Both kernels loop
+// over rows and columns with the block size, so either works.
+constexpr int SWEEP_MAX_THREADS = 512;
+constexpr int SWEEP_WIDE_BELOW = 608;   // fronts per level
+
 // The sweeps read the partitioned-inverse form written by k_block_inverse.
 // Dynamic shared memory of both: the front's dense vector v (f x NR entries)
 // followed by a 32 x NR staging area (placed there, aliasing v's buffer, so
@@ -573,7 +580,7 @@ template void numeric_factor<float>(FactorPlan &, const double *, const double *
 // solve remains.  Structure rows are added into the ancestors' entries
 // atomically (siblings share rows).
 template <class T, int NR>
-__global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+__global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_fwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
                                              const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
                                              int kcols, int c0) {
     extern __shared__ unsigned char smraw[];
@@ -684,7 +691,7 @@ __global__ void __launch_bounds__(256) k_fwd(const int *__restrict__ fronts, con
 // columns w, w + 8, ..., its lanes stride the rows with 8 loads in flight, and
 // a shuffle tree adds the lanes.  No serial triangular solve remains.
 template <class T, int NR>
-__global__ void __launch_bounds__(256) k_bwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+__global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
                                              const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
                                              int kcols, int c0) {
     extern __shared__ unsigned char smraw[];
@@ -806,13 +813,15 @@ static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c
         const Level &Lv = P.levels[dpt];
         if (Lv.fronts.empty()) continue;
         const size_t sm = sweep_dyn_smem<T, NR>(Lv.max_f);
-        k_fwd<T, NR><<<(unsigned)Lv.fronts.size(), 256, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+        const int nt = Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256;
+        k_fwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
     }
     for (int dpt = 0; dpt < nlev; ++dpt) {
         const Level &Lv = P.levels[dpt];
         if (Lv.fronts.empty()) continue;
         const size_t sm = sweep_dyn_smem<T, NR>(Lv.max_f);
-        k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), 256, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+        const int nt = Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256;
+        k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
     }
     GL_CUDA(cudaGetLastError());
 }
