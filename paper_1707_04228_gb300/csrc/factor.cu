@@ -562,11 +562,11 @@ template void numeric_factor<float>(FactorPlan &, const double *, const double *
 // ----------------------------------------------------------------- solves
 
 // Threads per CTA of the sweeps: 256, or 512 on levels with fewer fronts than
-// about four per SM (the upper dissection levels, large fronts), where one CTA
-// per front would otherwise leave most warp slots empty.  Both kernels loop
+// eight per SM (the upper dissection levels, large fronts), where one CTA per
+// front would otherwise leave most warp slots empty.  Both kernels loop
 // over rows and columns with the block size, so either works.
 constexpr int SWEEP_MAX_THREADS = 512;
-constexpr int SWEEP_WIDE_BELOW = 608;   // fronts per level
+constexpr int SWEEP_WIDE_BELOW = 1216;  // fronts per level
 
 // The sweeps read the partitioned-inverse form written by k_block_inverse.
 // Dynamic shared memory of both: the front's dense vector v (f x NR entries)
