@@ -20,7 +20,9 @@ corner_wide / corner_mixed (the 120x45x92 corner, 12,171,705 DOF, in FP64 or
 with FP32 local factors; --compare-fp64 adds the FP64 solve of the same
 laminate and reports the differences), batch (96 flat laminates solved
 together, autotuned decompositions) and adjoint (the gradient of the resin
-stress p-norm with respect to every element's misalignment angle).
+stress p-norm with respect to every element's misalignment angle) and
+paper_corner (the paper's 39-ply wrinkle-study geometry with its sech^2
+wrinkle, 13,559,865 DOF, mixed precision).
 
 --impl reference times the CPU oracle (oracle/), as it stands, on a bounded
 sample of the same laminate family on the host cores.
@@ -72,6 +74,13 @@ def workload(name):
         desc = ("curved_corner_120x45x92_q2: 12,171,705 DOF, 128 subdomains (32x4x1), 10 eigenvectors, "
                 + ("mixed (FP32 local factors and sweeps, FP64 CG/K*u/coarse), tol 1e-8" if mixed
                    else "FP64, tol 1e-10"))
+    elif name == "paper_corner":
+        lam = inputs.paper_corner()
+        lam.precision = 1
+        lam.tol = 1e-8
+        desc = ("paper_corner_120x60x77_q2: the 39-ply wrinkle-study geometry (R 22 mm, 10 mm limbs, 52 mm width, "
+                "0.24/0.015 mm plies/resin, sech^2 wrinkle of 0.62 mm), 13,559,865 DOF, 128 subdomains (32x4x1), "
+                "10 eigenvectors, mixed (FP32 local factors and sweeps), tol 1e-8")
     elif name == "corner_small":
         lam = inputs.curved_corner(n_arc=24, n_limb=4, n_width=8, nel_layer=1, name="curved_corner_small",
                                    nsub=(8, 2, 1), nev=10)

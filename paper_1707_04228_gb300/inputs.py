@@ -372,6 +372,41 @@ def corner_c1() -> Laminate:
     return curved_corner(name="curved_corner_120x30x92")
 
 
+# The 39-ply stacking sequence of the large corner study (Section 3):
+# [[-+45/90/0]_2/[-+45]_2/90/-+45/90/0/-+45/0/+-45/0/90/+-45/90/[+-45]_2/[0/90/+-45]_2]
+PAPER_39_PLY = ([-45, 45, 90, 0] * 2 + [-45, 45] * 2 + [90, -45, 45, 90, 0, -45, 45, 0, 45, -45, 0, 90, 45, -45, 90]
+                + [45, -45] * 2 + [0, 90, 45, -45] * 2)
+
+
+def paper_corner(n_arc=100, n_limb=10, n_width=60, d_wrinkle=0.62, delta=-1e-3, limb_bias=3.0,
+                 nsub=(32, 4, 1), nev=10, name=None) -> Laminate:
+    """The geometry of the paper's 39-ply wrinkle study (Section 3): inner radius
+    22 mm, 10 mm limbs, 52 mm width, 0.24 mm plies with 0.015 mm resin
+    interfaces (T = 9.93 mm), the printed stacking sequence, one Q2 element
+    through every ply and every interface (77 element layers), the sech^2
+    geometric wrinkle of amplitude d_wrinkle mm centred mid-arc, mid-width and
+    mid-thickness (0.62 mm gives a steepest fibre angle of about 10 degrees).
+    Loads as for the other corners: limb 1 clamped, a rigid opening rotation
+    of limb 2's end.  The paper's periodic width conditions and 3 mm edge
+    resin strips are not modelled.  Default mesh 120 x 60 x 77 elements,
+    13,559,865 DOF."""
+    assert len(PAPER_39_PLY) == 39
+    nel, th, mat, ang = _stack_with_resin(PAPER_39_PLY, 0.24, 0.015, 1, 1)
+    limb1 = graded(n_limb, -1.0, 0.0, limb_bias, fine_at_b=True) if n_limb else np.array([0.0])
+    arc = np.linspace(0.0, 1.0, n_arc + 1)
+    limb2 = graded(n_limb, 1.0, 2.0, limb_bias, fine_at_b=False) if n_limb else np.array([1.0])
+    sv = np.concatenate([limb1[:-1], arc, limb2[1:]])
+    lam = Laminate(name=name or f"paper_corner_{len(sv)-1}x{n_width}x{sum(nel)}", geometry=1,
+                   sv=sv, lv=np.linspace(0.0, 52.0, n_width + 1),
+                   layer_nel=nel, layer_thick=th, layer_mat=mat, layer_angle_deg=ang,
+                   materials=[PLY_T1, RESIN_T1], R_inner=22.0, limb_L=10.0, arc_deg=90.0,
+                   px=nsub[0], py=nsub[1], pz=nsub[2], overlap=1, nev=nev, tol=1e-10)
+    if d_wrinkle:
+        lam.node_dr, lam.theta = sech2_wrinkle(lam, d_wrinkle)
+    lam.dir_dof, lam.dir_val = merge_dirichlet(clamp_face(lam, FACE_SM), limb_end_rotation(lam, delta))
+    return lam
+
+
 def corner_mini(n_arc=8, n_limb=0, n_width=6, nel_layer=2, angles=(0, 90), nsub=(2, 2, 2), nev=8,
                 limb_L=5.0, width=6.0, amp_deg=10.0, wrinkle_w=1.0):
     """A small curved laminate of the same family, used for parity tests."""

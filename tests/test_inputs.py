@@ -32,3 +32,18 @@ def test_patch_mask_geometry_on_the_corner():
     assert not np.any(m & inputs.resin_elements(lam).reshape(m.shape))
     # arc length is continuous across the limb/arc joints and grows monotonically
     assert np.all(np.diff(s) > 0)
+
+
+def test_paper_corner_geometry():
+    """The 39-ply corner: the printed stack (39 plies, 38 resin interfaces,
+    T = 9.93 mm as the paper states), a wrinkle whose steepest fibre angle is
+    about 10 degrees, and no folded node column."""
+    lam = inputs.paper_corner()
+    plies = [a for a, m in zip(lam.layer_angle_deg, lam.layer_mat) if m == 0]
+    assert len(plies) == 39 and len(lam.layer_mat) == 77
+    assert abs(lam.thickness - 9.93) < 1e-9
+    assert sorted(set(plies)) == [-45.0, 0.0, 45.0, 90.0]
+    assert 9.0 < np.degrees(np.abs(lam.theta).max()) < 11.0
+    rn = inputs._q2_params(lam.rv())
+    assert np.diff(rn[:, None, None] + lam.node_dr, axis=0).min() > 0
+    assert lam.n_dof == 13_559_865
