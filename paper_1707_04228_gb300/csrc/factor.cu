@@ -941,23 +941,6 @@ int dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t
     return h;
 }
 
-// y = A x for symmetric A (n x n, column-major): warp per output reads column i.
-__global__ void k_symv(const double *__restrict__ A, int n, const double *__restrict__ x, double *__restrict__ y) {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const double *col = A + (int64_t)i * n;
-    double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += col[j] * x[j];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) y[i] = acc;
-}
-
-void dense_symv(const double *A, int n, const double *x, double *y, cudaStream_t s) {
-    k_symv<<<(n + 7) / 8, 256, 0, s>>>(A, n, x, y);
-    GL_CUDA(cudaGetLastError());
-}
-
 // Block-diagonal version: for each block b, y[o_b : o_b + n_b] = A_b x[o_b : o_b + n_b],
 // A_b stored column-major at aoff[b]; one warp per output row.
 __global__ void k_symv_blocks(const double *__restrict__ A, const int64_t *__restrict__ aoff,

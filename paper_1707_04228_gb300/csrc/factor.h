@@ -81,6 +81,5 @@ void dense_symv_blocks(const double *A, const int64_t *aoff, const int *voff, co
 // drop > 0: columns whose pivot on the unit-diagonal scale is <= drop are left
 // out (zero rows and columns in Ainv); returns how many were dropped.
 int dense_inverse(const double *A, int n, double *Ainv, int *d_err, cudaStream_t s, double drop = 0.0);
-void dense_symv(const double *A, int n, const double *x, double *y, cudaStream_t s);
 
 }  // namespace gl

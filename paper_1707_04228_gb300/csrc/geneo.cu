@@ -236,42 +236,6 @@ void fill_random(double *x, int64_t n, uint64_t seed, cudaStream_t s) {
     GL_CUDA(cudaGetLastError());
 }
 
-// out = alpha * (x - c * y) - z   (z may be NULL; out may alias x or z)
-__global__ void k_cheb_comb(double *out, const double *x, const double *y, const double *z, double alpha, double c,
-                            int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = alpha * (x[i] - c * y[i]);
-        if (z) v -= z[i];
-        out[i] = v;
-    }
-}
-
-void cheb_comb(double *out, const double *x, const double *y, const double *z, double alpha, double c, int64_t n,
-               cudaStream_t s) {
-    k_cheb_comb<<<2048, 256, 0, s>>>(out, x, y, z, alpha, c, n);
-    GL_CUDA(cudaGetLastError());
-}
-
-// Per-subdomain version: out = scale * ie_s * (x - c0_s * y) - z on multi-vectors of k columns.
-__global__ void k_cheb_comb_sub(const int64_t *__restrict__ voff, const int64_t *__restrict__ vlen, double *out,
-                                const double *x, const double *y, const double *z, double scale,
-                                const double *__restrict__ ie, const double *__restrict__ c0, int k) {
-    const int s = blockIdx.x;
-    const int64_t base = voff[s] * k, n = vlen[s] * k;
-    const double a = scale * ie[s], c = c0[s];
-    for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.y * blockDim.x) {
-        double v = a * (x[base + i] - c * y[base + i]);
-        if (z) v -= z[base + i];
-        out[base + i] = v;
-    }
-}
-
-void cheb_comb_sub(const FactorPlan &P, double *out, const double *x, const double *y, const double *z, double scale,
-                   const double *ie, const double *c0, int k, cudaStream_t s) {
-    k_cheb_comb_sub<<<dim3(P.n_sub, 64), 256, 0, s>>>(P.d_vec_off.p, P.d_vec_len.p, out, x, y, z, scale, ie, c0, k);
-    GL_CUDA(cudaGetLastError());
-}
-
 // ---------------------------------------------------------------- coarse restrict / prolong
 
 __global__ void __launch_bounds__(256) k_coarse_restrict(const int64_t *__restrict__ voff, const int64_t *__restrict__ vlen,

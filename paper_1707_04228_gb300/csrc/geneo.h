@@ -34,14 +34,6 @@ void small_geneig(int n_sub, int k, const double *GB, const double *GM, double *
 // X <- X Y per subdomain (k columns), using tmp of the same size.
 void local_rotate(const FactorPlan &P, double *X, const double *Y, int k, double *tmp, cudaStream_t s);
 
-// out = alpha * (x - c * y) - z elementwise (z may be NULL; out may alias x or z).
-void cheb_comb(double *out, const double *x, const double *y, const double *z, double alpha, double c, int64_t n,
-               cudaStream_t s);
-
-// Per subdomain s: out = scale * ie[s] * (x - c0[s] * y) - z (multi-vectors of k columns).
-void cheb_comb_sub(const FactorPlan &P, double *out, const double *x, const double *y, const double *z, double scale,
-                   const double *ie, const double *c0, int k, cudaStream_t s);
-
 // Deterministic pseudo-random fill of a multi-vector (splitmix64 hash of the index).
 void fill_random(double *x, int64_t n, uint64_t seed, cudaStream_t s);
 
