@@ -71,8 +71,6 @@ void gather_local(const FactorPlan &P, const double *r, T *xl, cudaStream_t s);
 template <class T>
 void scatter_add_local(const FactorPlan &P, const T *xl, double *z, cudaStream_t s);
 
-// Dense SPD matrix (n x n, column-major lower) factorised in place with the
-// same blocked kernels; solve with it.
 // Block-diagonal y = A x: block b (n_b rows, vector offset voff[b], matrix at aoff[b]).
 void dense_symv_blocks(const double *A, const int64_t *aoff, const int *voff, const int *nb, int nblk, int total,
                        const double *x, double *y, cudaStream_t s);
