@@ -84,6 +84,9 @@ typedef struct {
  *            fastest, then y, then z), or NULL.  The offset nodes must keep
  *            every through-thickness node column strictly increasing, else
  *            gl_set_mesh returns GL_ERR_INVALID_ARG.
+ *   elem_mat per-element material index (into the same table as layer_mat)
+ *            overriding the element's layer, length nx*ny*nz, or NULL: e.g.
+ *            resin strips along the free edges of the width (Section 3).
  * Material axes: R = R_l(psi + theta_e) R_r(phi), psi the frame angle at the
  * element centre (0 on limb 1 and flat plates), C_e constant per element. */
 typedef struct {
@@ -98,6 +101,7 @@ typedef struct {
     double R_inner, limb_L, arc_deg;
     const double *theta_e;
     const double *node_dr;
+    const int *elem_mat;
 } gl_mesh;
 
 /* Solver options.

@@ -244,6 +244,8 @@ class Mesh:
         self.conn = conn
         self.layer_of_elem = np.repeat(np.arange(len(lam.layer_nel)), lam.layer_nel)[ez]
         self.mat_of_elem = np.asarray(lam.layer_mat)[self.layer_of_elem]
+        if getattr(lam, "elem_mat", None) is not None:
+            self.mat_of_elem = np.asarray(lam.elem_mat).reshape(-1).astype(np.int64)
         tc = 0.5 * (np.asarray(lam.sv)[ex] + np.asarray(lam.sv)[ex + 1])
         self.psi = frame_angle(lam, tc)
         theta = np.zeros(self.n_elem) if lam.theta is None else np.asarray(lam.theta).reshape(-1)

@@ -32,12 +32,12 @@ __device__ void bond_pair(const double a[3][3], const double da[3][3], double M[
 
 // dC_e/dtheta_e (6x6, global axes) for element e.
 __device__ void dC_dtheta(int64_t e, int nx, int ny, const int *layer_of_ez, const int *layer_mat,
-                          const double *layer_angle, const double *theta, const double *psi_x, const double *matC,
-                          double dC[6][6]) {
+                          const int *elem_mat, const double *layer_angle, const double *theta, const double *psi_x,
+                          const double *matC, double dC[6][6]) {
     int ex = (int)(e % nx);
     int ez = (int)(e / ((int64_t)nx * ny));
     int layer = layer_of_ez[ez];
-    const double *Cm = matC + 36 * layer_mat[layer];
+    const double *Cm = matC + 36 * (elem_mat ? elem_mat[e] : layer_mat[layer]);
     double phi = layer_angle[layer];
     double a = psi_x[ex] + (theta ? theta[e] : 0.0);
     double ca = cos(a), sa = sin(a), cp = cos(phi), sp = sin(phi);
@@ -104,8 +104,9 @@ __device__ void inv3(const double J[3][3], double Ji[3][3]) {
 __global__ void k_stress_vjp(int64_t n_elem, int nx, int ny, int NX, int NY, const double *__restrict__ X,
                              const double *__restrict__ C, const double *__restrict__ psi_x,
                              const int *__restrict__ layer_of_ez, const int *__restrict__ layer_mat,
-                             const double *__restrict__ layer_angle, const double *__restrict__ theta,
-                             const double *__restrict__ matC, const double *__restrict__ u,
+                             const int *__restrict__ elem_mat, const double *__restrict__ layer_angle,
+                             const double *__restrict__ theta, const double *__restrict__ matC,
+                             const double *__restrict__ u,
                              const double *__restrict__ w33, const double *__restrict__ w13,
                              double *__restrict__ dJdu, double *__restrict__ dJdth) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -175,7 +176,7 @@ __global__ void k_stress_vjp(int64_t n_elem, int nx, int ny, int NX, int NY, con
             for (int d = 0; d < 3; ++d) H[c][d] = G[c][0] * Ji[0][d] + G[c][1] * Ji[1][d] + G[c][2] * Ji[2][d];
         double eps[6] = {H[0][0], H[1][1], H[2][2], H[1][2] + H[2][1], H[0][2] + H[2][0], H[0][1] + H[1][0]};
         double dC[6][6];
-        dC_dtheta(e, nx, ny, layer_of_ez, layer_mat, layer_angle, theta, psi_x, matC, dC);
+        dC_dtheta(e, nx, ny, layer_of_ez, layer_mat, elem_mat, layer_angle, theta, psi_x, matC, dC);
         double v = 0;
         for (int I = 0; I < 6; ++I)
             for (int K = 0; K < 6; ++K) v += wv[I] * dC[I][K] * eps[K];
@@ -186,15 +187,16 @@ __global__ void k_stress_vjp(int64_t n_elem, int nx, int ny, int NX, int NY, con
 // grad[e] = - sum_q w_q |J_q| eps(lambda)_q^T (dC_e/dtheta_e) eps(u)_q.  One thread per element.
 __global__ void k_adjoint_contract(int64_t n_elem, int nx, int ny, int NX, int NY, const double *__restrict__ geo,
                                    const int *__restrict__ layer_of_ez, const int *__restrict__ layer_mat,
-                                   const double *__restrict__ layer_angle, const double *__restrict__ theta,
-                                   const double *__restrict__ psi_x, const double *__restrict__ matC,
+                                   const int *__restrict__ elem_mat, const double *__restrict__ layer_angle,
+                                   const double *__restrict__ theta, const double *__restrict__ psi_x,
+                                   const double *__restrict__ matC,
                                    const double *__restrict__ u, const double *__restrict__ lam,
                                    double *__restrict__ grad) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n_elem) return;
     int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
     double dC[6][6];
-    dC_dtheta(e, nx, ny, layer_of_ez, layer_mat, layer_angle, theta, psi_x, matC, dC);
+    dC_dtheta(e, nx, ny, layer_of_ez, layer_mat, elem_mat, layer_angle, theta, psi_x, matC, dC);
     double maxd = 0;
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) maxd = fmax(maxd, fabs(dC[i][j]));
@@ -240,21 +242,21 @@ __global__ void k_adjoint_contract(int64_t n_elem, int nx, int ny, int NX, int N
 }
 
 void launch_stress_vjp(const MeshHost &m, const double *X, const double *C, const double *psi_x,
-                       const int *layer_of_ez, const int *layer_mat, const double *layer_angle, const double *theta,
-                       const double *matC, const double *u, const double *w33, const double *w13, double *dJdu,
-                       double *dJdth, cudaStream_t s) {
+                       const int *layer_of_ez, const int *layer_mat, const int *elem_mat, const double *layer_angle,
+                       const double *theta, const double *matC, const double *u, const double *w33, const double *w13,
+                       double *dJdu, double *dJdth, cudaStream_t s) {
     k_stress_vjp<<<(unsigned)((m.n_elem + 127) / 128), 128, 0, s>>>(m.n_elem, m.nx, m.ny, m.NX, m.NY, X, C, psi_x,
-                                                                   layer_of_ez, layer_mat, layer_angle, theta, matC, u,
-                                                                   w33, w13, dJdu, dJdth);
+                                                                   layer_of_ez, layer_mat, elem_mat, layer_angle,
+                                                                   theta, matC, u, w33, w13, dJdu, dJdth);
     GL_CUDA(cudaGetLastError());
 }
 
 void launch_adjoint_contract(const MeshHost &m, const double *geo, const int *layer_of_ez, const int *layer_mat,
-                             const double *layer_angle, const double *theta, const double *psi_x, const double *matC,
-                             const double *u, const double *lam, double *grad, cudaStream_t s) {
+                             const int *elem_mat, const double *layer_angle, const double *theta, const double *psi_x,
+                             const double *matC, const double *u, const double *lam, double *grad, cudaStream_t s) {
     k_adjoint_contract<<<(unsigned)((m.n_elem + 63) / 64), 64, 0, s>>>(m.n_elem, m.nx, m.ny, m.NX, m.NY, geo,
-                                                                      layer_of_ez, layer_mat, layer_angle, theta,
-                                                                      psi_x, matC, u, lam, grad);
+                                                                      layer_of_ez, layer_mat, elem_mat, layer_angle,
+                                                                      theta, psi_x, matC, u, lam, grad);
     GL_CUDA(cudaGetLastError());
 }
 

@@ -100,6 +100,7 @@ struct MeshHost {
     std::vector<double> layer_angle;         // rad
     std::vector<double> theta;               // per element (rad), may be empty
     std::vector<double> node_dr;             // per node through-thickness offset (mm), may be empty
+    std::vector<int> elem_mat;               // per element material overriding the layer's, may be empty
 };
 
 // ---------------------------------------------------------------- decomposition / symbolic
@@ -143,7 +144,7 @@ void build_symbolic(const MeshHost &m, const SubBox &b, const std::vector<uint8_
 void launch_node_coords(const MeshHost &m, const double *tn, const double *ln, const double *rn,
                         const double *dr, double *X, cudaStream_t s);
 void launch_elem_material(int64_t n_elem, int nx, int ny, const int *layer_of_ez, const int *layer_mat,
-                          const double *layer_angle, const double *theta, const double *psi,
+                          const int *elem_mat, const double *layer_angle, const double *theta, const double *psi,
                           const double *matC, double *C, cudaStream_t s);
 void launch_elem_geometry(const MeshHost &m, const double *X, double *geo, cudaStream_t s);
 void launch_traction(const MeshHost &m, const double *X, int face, const double t[3], double *f,
@@ -159,11 +160,11 @@ void launch_failure(const MeshHost &m, const double *X, const double *C, const d
 void stress_noalloc(const MeshHost &m, int device, const double *X, const double *C, const double *psi_x,
                     const uint8_t *resin, const double *u, double *s33, double *t13, double *peak, cudaStream_t s);
 void launch_stress_vjp(const MeshHost &m, const double *X, const double *C, const double *psi_x,
-                       const int *layer_of_ez, const int *layer_mat, const double *layer_angle, const double *theta,
-                       const double *matC, const double *u, const double *w33, const double *w13, double *dJdu,
-                       double *dJdth, cudaStream_t s);
+                       const int *layer_of_ez, const int *layer_mat, const int *elem_mat, const double *layer_angle,
+                       const double *theta, const double *matC, const double *u, const double *w33, const double *w13,
+                       double *dJdu, double *dJdth, cudaStream_t s);
 void launch_adjoint_contract(const MeshHost &m, const double *geo, const int *layer_of_ez, const int *layer_mat,
-                             const double *layer_angle, const double *theta, const double *psi_x, const double *matC,
-                             const double *u, const double *lam, double *grad, cudaStream_t s);
+                             const int *elem_mat, const double *layer_angle, const double *theta, const double *psi_x,
+                             const double *matC, const double *u, const double *lam, double *grad, cudaStream_t s);
 
 }  // namespace gl

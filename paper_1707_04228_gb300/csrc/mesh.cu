@@ -69,8 +69,10 @@ __device__ void bond_matrix(const double a[3][3], double M[6][6]) {
     }
 }
 
+// elem_mat (may be NULL): per-element material index overriding the layer's.
 __global__ void k_elem_material(int64_t n_elem, int nx, int ny, const int *__restrict__ layer_of_ez,
-                                const int *__restrict__ layer_mat, const double *__restrict__ layer_angle,
+                                const int *__restrict__ layer_mat, const int *__restrict__ elem_mat,
+                                const double *__restrict__ layer_angle,
                                 const double *__restrict__ theta, const double *__restrict__ psi_x,
                                 const double *__restrict__ matC, double *__restrict__ C) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -78,7 +80,7 @@ __global__ void k_elem_material(int64_t n_elem, int nx, int ny, const int *__res
     int ex = (int)(e % nx);
     int ez = (int)(e / ((int64_t)nx * ny));
     int layer = layer_of_ez[ez];
-    int mat = layer_mat[layer];
+    int mat = elem_mat ? elem_mat[e] : layer_mat[layer];
     double phi = layer_angle[layer];
     double a = psi_x[ex] + (theta ? theta[e] : 0.0);
     double Ry[3][3];
@@ -111,10 +113,10 @@ __global__ void k_elem_material(int64_t n_elem, int nx, int ny, const int *__res
 }
 
 void launch_elem_material(int64_t n_elem, int nx, int ny, const int *layer_of_ez, const int *layer_mat,
-                          const double *layer_angle, const double *theta, const double *psi_x,
+                          const int *elem_mat, const double *layer_angle, const double *theta, const double *psi_x,
                           const double *matC, double *C, cudaStream_t s) {
     k_elem_material<<<(unsigned)((n_elem + 127) / 128), 128, 0, s>>>(n_elem, nx, ny, layer_of_ez, layer_mat,
-                                                                    layer_angle, theta, psi_x, matC, C);
+                                                                    elem_mat, layer_angle, theta, psi_x, matC, C);
     GL_CUDA(cudaGetLastError());
 }
 

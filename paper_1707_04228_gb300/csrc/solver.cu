@@ -109,7 +109,7 @@ struct gl_ctx {
     std::vector<double> psi_x;
     // device mesh data
     DBuf<double> d_tn, d_ln, d_rn, d_dr, d_X, d_C, d_geo, d_psi, d_theta, d_layer_angle, d_matC;
-    DBuf<int> d_layer_of_ez, d_layer_mat;
+    DBuf<int> d_layer_of_ez, d_layer_mat, d_elem_mat;
     DBuf<uint8_t> d_resin;
     // boundary data
     std::vector<int64_t> dir_dof;
@@ -221,16 +221,18 @@ void build_geometry(gl_ctx *c) {
     c->d_layer_angle.upload(m.layer_angle, s);
     if (!m.theta.empty()) c->d_theta.upload(m.theta, s);
     else c->d_theta.release();
+    if (!m.elem_mat.empty()) c->d_elem_mat.upload(m.elem_mat, s);
+    else c->d_elem_mat.release();
     c->d_matC.upload(c->matC, s);
     c->d_C.alloc(36 * m.n_elem);
-    launch_elem_material(m.n_elem, m.nx, m.ny, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_layer_angle.p,
-                         c->d_theta.p, c->d_psi.p, c->d_matC.p, c->d_C.p, s);
+    launch_elem_material(m.n_elem, m.nx, m.ny, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
+                         c->d_layer_angle.p, c->d_theta.p, c->d_psi.p, c->d_matC.p, c->d_C.p, s);
     c->d_geo.alloc(270 * m.n_elem);
     launch_elem_geometry(m, c->d_X.p, c->d_geo.p, s);
     std::vector<uint8_t> resin(m.n_elem);
     for (int64_t e = 0; e < m.n_elem; ++e) {
         int ez = (int)(e / ((int64_t)m.nx * m.ny));
-        resin[e] = c->mat_iso[m.layer_mat[m.layer_of_ez[ez]]];
+        resin[e] = c->mat_iso[m.elem_mat.empty() ? m.layer_mat[m.layer_of_ez[ez]] : m.elem_mat[e]];
     }
     c->d_resin.upload(resin, s);
     c->d_ftrac.alloc(m.n_dof);
@@ -1084,6 +1086,11 @@ int gl_set_mesh(gl_ctx *c, const gl_mesh *mesh) {
         m.ln = mid(m.lv);
         m.rn = mid(m.rv);
         if (mesh->theta_e) m.theta = fetch(mesh->theta_e, m.n_elem);
+        if (mesh->elem_mat) {
+            m.elem_mat = fetch(mesh->elem_mat, m.n_elem);
+            for (int v : m.elem_mat)
+                GL_REQUIRE(v >= 0 && v < (int)c->mat_iso.size(), "element material out of range");
+        }
         if (mesh->node_dr) {
             m.node_dr = fetch(mesh->node_dr, m.n_nodes);
             // every through-thickness node column must stay strictly increasing
@@ -1292,8 +1299,8 @@ int gl_set_theta(gl_ctx *c, const double *theta_e) {
         if (c->ready) {
             // new C_e for K u and the stresses; the factors and the coarse space are kept
             c->d_theta.upload(m.theta, c->stream);
-            launch_elem_material(m.n_elem, m.nx, m.ny, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_layer_angle.p,
-                                 c->d_theta.p, c->d_psi.p, c->d_matC.p, c->d_C.p, c->stream);
+            launch_elem_material(m.n_elem, m.nx, m.ny, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
+                                 c->d_layer_angle.p, c->d_theta.p, c->d_psi.p, c->d_matC.p, c->d_C.p, c->stream);
             GL_CUDA(cudaStreamSynchronize(c->stream));
         }
     });
@@ -1322,7 +1329,7 @@ int gl_stress_vjp(gl_ctx *c, const double *u, const double *w33, const double *w
             dgu.zero(s);
         }
         if (dJdth) dgt.alloc(m.n_elem);
-        launch_stress_vjp(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_layer_of_ez.p, c->d_layer_mat.p,
+        launch_stress_vjp(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
                           c->d_layer_angle.p, c->d_theta.p, c->d_matC.p, du.p, d33.p, d13.p, dgu.p, dgt.p, s);
         g_launches += 1;
         if (dJdu) from_device(dJdu, dgu.p, m.n_dof, s);
@@ -1344,7 +1351,8 @@ int gl_adjoint(gl_ctx *c, const double *u, const double *dJdu, double *grad, gl_
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
         dg.alloc(m.n_elem);
-        launch_adjoint_contract(m, c->d_geo.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_layer_angle.p,
+        launch_adjoint_contract(m, c->d_geo.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
+                                c->d_layer_angle.p,
                                 c->d_theta.p, c->d_psi.p, c->d_matC.p, du.p, lam.p, dg.p, s);
         g_launches += 1;
         from_device(grad, dg.p, m.n_elem, s);

@@ -57,6 +57,7 @@ class Laminate:
     arc_deg: float = 90.0
     theta: np.ndarray | None = None   # (nz, ny, nx) misalignment, rad
     node_dr: np.ndarray | None = None  # (NZ, NY, NX) through-thickness node offset (geometric wrinkle), mm
+    elem_mat: np.ndarray | None = None  # (nz, ny, nx) material index overriding the layer's (edge resin strips)
     dir_dof: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     dir_val: np.ndarray = field(default_factory=lambda: np.zeros(0))
     traction: list = field(default_factory=list)   # [(face, (tx, ty, tz))] MPa, global axes
@@ -195,9 +196,12 @@ def centre_arc_length(lam: Laminate):
 
 
 def resin_elements(lam: Laminate):
-    """Boolean per element (element order x fastest, then y, then z): isotropic resin layer."""
-    iso = np.array([lam.materials[m]["kind"] == "iso" for m in lam.layer_mat])
-    ez = iso[lam.elem_layer()]
+    """Boolean per element (element order x fastest, then y, then z): isotropic resin
+    (its layer's material, or its own where elem_mat overrides it)."""
+    iso_of_mat = np.array([m["kind"] == "iso" for m in lam.materials])
+    if lam.elem_mat is not None:
+        return iso_of_mat[np.asarray(lam.elem_mat).reshape(-1)]
+    ez = iso_of_mat[np.asarray(lam.layer_mat)][lam.elem_layer()]
     return np.broadcast_to(ez[:, None, None], (lam.nz, lam.ny, lam.nx)).reshape(-1).copy()
 
 
@@ -234,7 +238,7 @@ def _q2_params(v):
 
 
 def sech2_wrinkle(lam: Laminate, d, b1=0.2, b2_inner=0.5, b2_outer=0.25, b3=0.5,
-                  s_def=None, l_def=None, r_def=None):
+                  s_def=None, l_def=None, r_def=None, width=None):
     """The paper's geometric wrinkle (Section 3, Eqs. eq-wrinkle and eq-f):
     the through-thickness coordinate of every node moves by
 
@@ -247,9 +251,10 @@ def sech2_wrinkle(lam: Laminate, d, b1=0.2, b2_inner=0.5, b2_outer=0.25, b3=0.5,
     fibres follow the wrinkled surfaces: theta_e = -atan(df/ds) at the element
     centre (s the arc length of the ply at that depth; R_l(theta) tilts e_s
     towards -r for theta > 0).  Returns (node_dr (NZ, NY, NX), theta (nz, ny, nx));
-    defaults centre the defect mid-arc, mid-width and mid-thickness."""
+    defaults centre the defect mid-arc, mid-width and mid-thickness; width
+    (default: the mesh's) is the part width W of the l factor."""
     T = lam.thickness
-    W = float(lam.lv[-1] - lam.lv[0])
+    W = float(lam.lv[-1] - lam.lv[0]) if width is None else float(width)
     sv = np.asarray(lam.sv, dtype=np.float64)
     if lam.geometry == 1:
         to_s = lambda t: t                                  # arc parameter
@@ -379,7 +384,7 @@ PAPER_39_PLY = ([-45, 45, 90, 0] * 2 + [-45, 45] * 2 + [90, -45, 45, 90, 0, -45,
 
 
 def paper_corner(n_arc=100, n_limb=10, n_width=60, d_wrinkle=0.62, delta=-1e-3, limb_bias=3.0,
-                 nsub=(32, 4, 1), nev=10, name=None) -> Laminate:
+                 nsub=(32, 4, 1), nev=10, edge_resin=0.0, n_edge=2, name=None) -> Laminate:
     """The geometry of the paper's 39-ply wrinkle study (Section 3): inner radius
     22 mm, 10 mm limbs, 52 mm width, 0.24 mm plies with 0.015 mm resin
     interfaces (T = 9.93 mm), the printed stacking sequence, one Q2 element
@@ -387,22 +392,32 @@ def paper_corner(n_arc=100, n_limb=10, n_width=60, d_wrinkle=0.62, delta=-1e-3, 
     geometric wrinkle of amplitude d_wrinkle mm centred mid-arc, mid-width and
     mid-thickness (0.62 mm gives a steepest fibre angle of about 10 degrees).
     Loads as for the other corners: limb 1 clamped, a rigid opening rotation
-    of limb 2's end.  The paper's periodic width conditions and 3 mm edge
-    resin strips are not modelled.  Default mesh 120 x 60 x 77 elements,
-    13,559,865 DOF."""
+    of limb 2's end.  edge_resin > 0 adds the paper's resin strips of that
+    width (mm, n_edge elements each) along both free edges of the width (all
+    layers resin there); the periodic width conditions are not modelled.
+    Default mesh 120 x 60 x 77 elements, 13,559,865 DOF."""
     assert len(PAPER_39_PLY) == 39
     nel, th, mat, ang = _stack_with_resin(PAPER_39_PLY, 0.24, 0.015, 1, 1)
     limb1 = graded(n_limb, -1.0, 0.0, limb_bias, fine_at_b=True) if n_limb else np.array([0.0])
     arc = np.linspace(0.0, 1.0, n_arc + 1)
     limb2 = graded(n_limb, 1.0, 2.0, limb_bias, fine_at_b=False) if n_limb else np.array([1.0])
     sv = np.concatenate([limb1[:-1], arc, limb2[1:]])
-    lam = Laminate(name=name or f"paper_corner_{len(sv)-1}x{n_width}x{sum(nel)}", geometry=1,
-                   sv=sv, lv=np.linspace(0.0, 52.0, n_width + 1),
+    lv = np.linspace(0.0, 52.0, n_width + 1)
+    if edge_resin > 0:
+        strip = np.linspace(0.0, edge_resin, n_edge + 1)
+        lv = np.concatenate([strip[:-1] - edge_resin, lv, 52.0 + strip[1:]])
+    lam = Laminate(name=name or f"paper_corner_{len(sv)-1}x{len(lv)-1}x{sum(nel)}", geometry=1,
+                   sv=sv, lv=lv,
                    layer_nel=nel, layer_thick=th, layer_mat=mat, layer_angle_deg=ang,
                    materials=[PLY_T1, RESIN_T1], R_inner=22.0, limb_L=10.0, arc_deg=90.0,
                    px=nsub[0], py=nsub[1], pz=nsub[2], overlap=1, nev=nev, tol=1e-10)
+    if edge_resin > 0:
+        em = np.broadcast_to(np.asarray(mat)[lam.elem_layer()][:, None, None], (lam.nz, lam.ny, lam.nx)).copy()
+        em[:, :n_edge, :] = 1
+        em[:, -n_edge:, :] = 1
+        lam.elem_mat = em
     if d_wrinkle:
-        lam.node_dr, lam.theta = sech2_wrinkle(lam, d_wrinkle)
+        lam.node_dr, lam.theta = sech2_wrinkle(lam, d_wrinkle, width=52.0)
     lam.dir_dof, lam.dir_val = merge_dirichlet(clamp_face(lam, FACE_SM), limb_end_rotation(lam, delta))
     return lam
 

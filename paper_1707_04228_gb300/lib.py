@@ -36,7 +36,7 @@ class gl_mesh(C.Structure):
                 ("nlayers", C.c_int), ("layer_nel", C.c_void_p), ("layer_thick", C.c_void_p),
                 ("layer_mat", C.c_void_p), ("layer_angle_deg", C.c_void_p), ("geometry", C.c_int),
                 ("R_inner", C.c_double), ("limb_L", C.c_double), ("arc_deg", C.c_double),
-                ("theta_e", C.c_void_p), ("node_dr", C.c_void_p)]
+                ("theta_e", C.c_void_p), ("node_dr", C.c_void_p), ("elem_mat", C.c_void_p)]
 
 
 class gl_opts(C.Structure):
@@ -187,13 +187,16 @@ class Solver:
         theta = None if lam.theta is None else np.ascontiguousarray(np.asarray(lam.theta).reshape(-1), dtype=np.float64)
         dr = getattr(lam, "node_dr", None)
         dr = None if dr is None else np.ascontiguousarray(np.asarray(dr).reshape(-1), dtype=np.float64)
-        self._keep = [x, y, nel, th, mat, ang, theta, dr]
+        em = getattr(lam, "elem_mat", None)
+        em = None if em is None else np.ascontiguousarray(np.asarray(em).reshape(-1), dtype=np.int32)
+        self._keep = [x, y, nel, th, mat, ang, theta, dr, em]
         m = gl_mesh(nx=len(x) - 1, ny=len(y) - 1, x=x.ctypes.data, y=y.ctypes.data, nlayers=len(nel),
                     layer_nel=nel.ctypes.data, layer_thick=th.ctypes.data, layer_mat=mat.ctypes.data,
                     layer_angle_deg=ang.ctypes.data, geometry=int(lam.geometry), R_inner=float(lam.R_inner),
                     limb_L=float(lam.limb_L), arc_deg=float(lam.arc_deg),
                     theta_e=None if theta is None else theta.ctypes.data,
-                    node_dr=None if dr is None else dr.ctypes.data)
+                    node_dr=None if dr is None else dr.ctypes.data,
+                    elem_mat=None if em is None else em.ctypes.data)
         _check(self.lib, self.lib.gl_set_mesh(self.ctx, C.byref(m)))
 
     def set_dirichlet(self, dof, val):

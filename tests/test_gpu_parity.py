@@ -250,3 +250,42 @@ def test_folding_wrinkle_is_rejected(lib_mod):
     with pytest.raises(lib_mod.GLError) as e:
         lib_mod.Solver.from_laminate(lam)
     assert e.value.code == -1
+
+
+def edge_resin_corner():
+    """Mini curved corner whose outermost element columns across the width are
+    resin in every layer (per-element materials, as the paper's edge strips)."""
+    lam = inputs.corner_mini(n_arc=6, n_limb=1, n_width=5, nel_layer=1, angles=(0, 45, 90), nsub=(3, 1, 1), nev=8,
+                             limb_L=2.0, width=5.0)
+    em = np.broadcast_to(np.asarray(lam.layer_mat)[lam.elem_layer()][:, None, None], (lam.nz, lam.ny, lam.nx)).copy()
+    em[:, 0, :] = 1
+    em[:, -1, :] = 1
+    lam.elem_mat = em
+    return lam
+
+
+def test_edge_resin_corner_matches_oracle(lib_mod):
+    import torch
+    from oracle import adjoint
+    from paper_1707_04228_gb300.autograd import pnorm, stress_of_theta
+    lam = edge_resin_corner()
+    mesh = fem.Mesh(lam)
+    sysm = fem.System(mesh)
+    assert mesh.is_resin.reshape(lam.nz, lam.ny, lam.nx)[:, 0, :].all()
+    s = lib_mod.Solver.from_laminate(lam, tol=1e-12)
+    x = inputs.random_vector(mesh.n_dof, 19)
+    assert rel(s.apply_K(x), sysm.K @ x) <= 1e-12
+    u_ref = sysm.direct()
+    u, info = s.solve()
+    assert info["status"] == 0 and rel(u, u_ref) <= 1e-8
+    _, _, peak = s.stress(u)
+    r33, _ = fem.stress_slr(mesh, u_ref)
+    assert abs(peak - r33[mesh.is_resin].max()) <= 1e-6 * np.abs(r33).max()
+    # the adjoint contraction reads the same per-element materials
+    mask = inputs.arc_resin_mask(lam) & mesh.is_resin
+    theta = torch.tensor(mesh.theta, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = pnorm(stress_of_theta(theta, s), torch.tensor(mask, device="cuda"), 8)
+    J.backward()
+    J_ref, g_ref, _ = adjoint.gradient(sysm, mask, 8)
+    assert abs(J.item() - J_ref) <= 1e-9 * J_ref
+    assert np.abs(theta.grad.cpu().numpy() - g_ref).max() <= 1e-6 * np.abs(g_ref).max()

@@ -47,3 +47,13 @@ def test_paper_corner_geometry():
     rn = inputs._q2_params(lam.rv())
     assert np.diff(rn[:, None, None] + lam.node_dr, axis=0).min() > 0
     assert lam.n_dof == 13_559_865
+
+
+def test_paper_corner_edge_resin_strips():
+    lam = inputs.paper_corner(n_arc=6, n_limb=1, n_width=4, edge_resin=3.0, n_edge=2, nsub=(2, 2, 1))
+    assert np.allclose(lam.lv[[0, 2, -3, -1]], [-3.0, 0.0, 52.0, 55.0])
+    em = lam.elem_mat
+    assert em.shape == (lam.nz, lam.ny, lam.nx)
+    assert np.all(em[:, :2, :] == 1) and np.all(em[:, -2:, :] == 1)
+    inner = em[:, 2:-2, :]
+    assert np.array_equal(inner[:, 0, 0], np.asarray(lam.layer_mat)[lam.elem_layer()])
