@@ -19,6 +19,7 @@
 // backward, each block step a plain product with that form.
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "factor.h"
 #include "q2.cuh"
@@ -29,6 +30,26 @@ constexpr int NB = 32;        // pivot block
 constexpr int TILE = 64;      // trailing-update tile
 
 // ----------------------------------------------------------------- plan
+
+// A kernel's dynamic shared-memory limit is an attribute of the device that
+// is current when it is set, so the limit already raised is kept per device.
+struct SmemLimit {
+    static constexpr int MAX_DEVICES = 64;
+    std::mutex mu;
+    size_t set[MAX_DEVICES] = {};
+};
+
+template <class F>
+static void raise_smem_limit(SmemLimit &L, size_t need, F apply) {
+    int dev = 0;
+    GL_CUDA(cudaGetDevice(&dev));
+    GL_REQUIRE(dev >= 0 && dev < SmemLimit::MAX_DEVICES, "device index out of range");
+    std::lock_guard<std::mutex> lock(L.mu);
+    if (need > L.set[dev]) {
+        apply(need);
+        L.set[dev] = need;
+    }
+}
 
 void sweep_smem_for_plan(int max_f);
 
@@ -452,11 +473,10 @@ __global__ void __launch_bounds__(256) k_block_inverse(const FrontDesc *__restri
 template <class T>
 void numeric_factor(FactorPlan &P, const double *C, const double *geo, const double *xi, double sigma, T *L,
                     int *d_err, cudaStream_t s) {
-    static bool smem_set = false;
-    if (!smem_set) {
-        GL_CUDA(cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 6561 * 8));
-        smem_set = true;
-    }
+    static SmemLimit assemble_smem;
+    raise_smem_limit(assemble_smem, 6561 * 8, [](size_t v) {
+        GL_CUDA(cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
+    });
     const int nlev = (int)P.levels.size();
     const int64_t budget = (int64_t)(6e9 / sizeof(T));   // entries per workspace buffer
     std::vector<int> depth_of(P.fr.size());
@@ -757,20 +777,19 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict
 }
 
 // Shared memory of the sweeps: static tiles plus the dynamic front vector and
-// staging area.  The dynamic limit is raised per kernel to the largest front
+// staging area.  The dynamic limit is raised per kernel and device to the largest front
 // seen; build_plan calls sweep_smem_for_plan for every variant, so no
 // attribute is ever changed while a stream is being captured.
 constexpr size_t SMEM_PER_CTA = 227 * 1024;
 
 template <class T, int NR>
 static size_t sweep_static_smem() {
-    static size_t v = 0;
-    if (!v) {
+    static const size_t v = [] {
         cudaFuncAttributes a{}, b{};
         GL_CUDA(cudaFuncGetAttributes(&a, k_fwd<T, NR>));
         GL_CUDA(cudaFuncGetAttributes(&b, k_bwd<T, NR>));
-        v = std::max<size_t>(1, std::max(a.sharedSizeBytes, b.sharedSizeBytes));
-    }
+        return std::max<size_t>(1, std::max(a.sharedSizeBytes, b.sharedSizeBytes));
+    }();
     return v;
 }
 
@@ -786,14 +805,12 @@ static bool sweep_fits(int max_f) {
 
 template <class T, int NR>
 static void ensure_sweep_smem(int max_f) {
-    static size_t attr_set = 0;
+    static SmemLimit limit;
     if (!sweep_fits<T, NR>(max_f)) return;
-    const size_t smem = sweep_dyn_smem<T, NR>(max_f);
-    if (smem > attr_set) {
-        GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = smem;
-    }
+    raise_smem_limit(limit, sweep_dyn_smem<T, NR>(max_f), [](size_t v) {
+        GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
+        GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
+    });
 }
 
 void sweep_smem_for_plan(int max_f) {
