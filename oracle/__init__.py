@@ -14,6 +14,10 @@ Modules
   geneo  -- overlapping decomposition, partition of unity, local Dirichlet and
             Neumann matrices, GenEO eigenproblems, coarse space, additive
             two-level Schwarz, PCG (Section 2.3).
+  adjoint -- adjoint gradient of the resin stress p-norm with respect to the
+            misalignment angles, by direct solves (Section 3).
+  serendipity -- the 20-node serendipity hexahedron of the paper's own code
+            (Section 2.1) on the same laminates; no GPU counterpart yet.
 
 Every function cites the passage it follows.  Where the paper is silent the
 docstring says which reading is taken.  Parity unpinned: none of the paper's
