@@ -402,6 +402,37 @@ class System:
         return self.full(uf)
 
 
+def periodic_width_direct(mesh, dir_dof, dir_val, f=None, K=None):
+    """Direct solve with periodic width conditions, u(s, 0, r) = u(s, W, r), as in
+    the paper's 39-ply study (Section 3).  Every node of the last width plane
+    (iy = NY - 1) is identified with its partner on the first (iy = 0): with A
+    the n_dof x n_master selection matrix, K_p = A^T K A and f_p = A^T f;
+    Dirichlet DOFs are given in full-mesh numbering (a DOF on the last plane
+    stands for its partner).  Returns the full displacement (both planes carry
+    the same values)."""
+    n = mesh.n_dof
+    K = assemble_K(mesh) if K is None else K
+    f = load_vector(mesh) if f is None else f
+    node = np.arange(mesh.n_nodes)
+    iy = (node // mesh.NX) % mesh.NY
+    rep_node = np.where(iy == mesh.NY - 1, node - (mesh.NY - 1) * mesh.NX, node)
+    rep = (3 * rep_node[:, None] + np.arange(3)[None, :]).ravel()       # DOF -> its master DOF
+    masters = np.unique(rep)
+    col = -np.ones(n, dtype=np.int64)
+    col[masters] = np.arange(masters.size)
+    A = sp.csr_matrix((np.ones(n), (np.arange(n), col[rep])), shape=(n, masters.size))
+    Kp = (A.T @ K @ A).tocsr()
+    fp = A.T @ f
+    # a DOF on the last plane and its partner may both be listed: keep each master once
+    d, first = np.unique(col[rep[np.asarray(dir_dof, dtype=np.int64)]], return_index=True)
+    up = np.zeros(masters.size)
+    up[d] = np.asarray(dir_val, dtype=np.float64)[first]
+    free = np.setdiff1d(np.arange(masters.size), d)
+    rhs = fp[free] - Kp[free][:, d] @ up[d]
+    up[free] = spla.splu(Kp[free][:, free].tocsc()).solve(rhs)
+    return A @ up
+
+
 # --------------------------------------------------------------------------
 # Stress recovery (Section 2.2 notation sigma_r, tau_rs; Eq. eq-Camanho uses them).
 # --------------------------------------------------------------------------

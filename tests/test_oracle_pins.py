@@ -286,6 +286,28 @@ def test_tip_loaded_cantilever_approaches_timoshenko():
     assert abs(tips[1] / tips[0] - 1.0) <= 0.005
 
 
+def test_periodic_width_gives_generalised_plane_strain():
+    """Periodic width conditions (the paper's 39-ply study, Section 3) on a
+    homogeneous isotropic strip stretched along x: periodicity forbids a mean
+    width strain, so the exact field is u = (eps x, 0, -nu/(1-nu) eps z), which
+    Q2 reproduces; the same strip with free width faces contracts by -nu eps."""
+    E, nu, eps, L, W, H = 10000.0, 0.3, 1e-3, 3.0, 2.0, 0.8
+    iso = dict(kind="iso", E=E, nu=nu)
+    lam = block(3, 2, [(2, H, 0, 0.0)], sx=L, sy=W, mats=[iso])
+    mesh = fem.Mesh(lam)
+    X = mesh.X
+    ends = np.flatnonzero(np.isclose(X[:, 0], 0.0) | np.isclose(X[:, 0], L))
+    corner = np.flatnonzero(np.all(np.isclose(X, 0.0), axis=1))
+    above = np.flatnonzero(np.all(np.isclose(X, [0.0, 0.0, H]), axis=1))   # stops the rotation about x
+    dof = np.concatenate([3 * ends, 3 * corner + 1, 3 * corner + 2, 3 * above + 1])
+    val = np.concatenate([eps * X[ends, 0], [0.0], [0.0], [0.0]])
+    u = fem.periodic_width_direct(mesh, dof, val, f=np.zeros(mesh.n_dof)).reshape(-1, 3)
+    exact = np.stack([eps * X[:, 0], 0.0 * X[:, 0], -nu / (1 - nu) * eps * X[:, 2]], axis=1)
+    assert np.abs(u - exact).max() <= 1e-12 * eps * L
+    free = fem.System(mesh, f=np.zeros(mesh.n_dof), dir_dof=dof, dir_val=val).direct().reshape(-1, 3)
+    assert np.allclose(free[:, 1], -nu * eps * X[:, 1], atol=1e-12)
+
+
 def test_clt_laminate_in_plane_strain_exact():
     """[0/R/90/R/90/R/0] under in-plane strain: per-layer plane stress, reproduced exactly.
 
