@@ -353,6 +353,37 @@ def test_clt_laminate_in_plane_strain_exact():
     assert np.abs(t13).max() < 1e-8 * np.abs(sx_exact).max()
 
 
+def test_free_edge_plate_modulus_near_clt():
+    """The [0/R/90/R/90/R/0] plate stretched along x with free width and thickness
+    faces: its axial stiffness F/(eps W) is the CLT membrane stiffness
+    A11 - A12^2/A22 up to free-edge effects of about a percent."""
+    c0 = inputs.flat_plate_c0()
+    layers = list(zip([1] * 7, c0.layer_thick, c0.layer_mat, c0.layer_angle_deg))
+    L = W = 20.0
+    lam = block(8, 8, layers, sx=L, sy=W)
+    Cply = fem.orthotropic_C(**inputs.PLY_T1)
+    perm = [1, 0, 2, 4, 3, 5]
+    Cl = {0.0: Cply, 90.0: Cply[np.ix_(perm, perm)]}
+    Ciso = fem.isotropic_C(**inputs.RESIN_T1)
+    Cs = [Ciso if m == 1 else Cl[a] for m, a in zip(lam.layer_mat, lam.layer_angle_deg)]
+    Qb = [C[:2, :2] - np.outer(C[:2, 2], C[2, :2]) / C[2, 2] for C in Cs]
+    A = sum(Q * h for Q, h in zip(Qb, lam.layer_thick))
+    a_clt = A[0, 0] - A[0, 1] ** 2 / A[1, 1]
+    mesh = fem.Mesh(lam)
+    X = mesh.X
+    eps = 1e-3
+    ends = np.flatnonzero(np.isclose(X[:, 0], 0.0) | np.isclose(X[:, 0], L))
+    o = np.flatnonzero(np.all(np.isclose(X, 0.0), axis=1))
+    oy = np.flatnonzero(np.all(np.isclose(X, [0.0, W, 0.0]), axis=1))
+    dof = np.concatenate([3 * ends, 3 * o + 1, 3 * o + 2, 3 * oy + 2])
+    val = np.concatenate([eps * X[ends, 0], [0.0, 0.0, 0.0]])
+    sysm = fem.System(mesh, f=np.zeros(mesh.n_dof), dir_dof=dof, dir_val=val)
+    u = sysm.direct()
+    far = np.flatnonzero(np.isclose(X[:, 0], L))
+    F = (sysm.K @ u)[3 * far].sum()
+    assert abs(F / (eps * W) / a_clt - 1.0) <= 0.03
+
+
 def test_rigid_rotation_gives_zero_stress_on_curved_mesh():
     lam = inputs.corner_mini(n_arc=4, n_limb=1, n_width=2, nel_layer=1)
     mesh = fem.Mesh(lam)
