@@ -117,12 +117,26 @@ typedef struct {
  *   sigma      shift of the definite GenEO pencil (eigenvectors do not
  *              depend on it); <= 0 selects 1e-3.
  *   eig_iters  cap on the subspace iterations of the GenEO eigensolver
- *              (<= 0: 100); it stops earlier once the kept Ritz values of
- *              every subdomain change by less than 1e-14 (relative). */
+ *              (<= 0: 100); after at least 4 iterations it stops once the
+ *              kept Ritz values of every subdomain change by less than 1e-10
+ *              (relative) between iterations.
+ *   factor_ws_bytes  device workspace per buffer of the numeric
+ *              factorisation (two buffers hold the dense fronts of two
+ *              adjacent dissection levels); subdomains are factored in
+ *              consecutive groups that fit it.  <= 0 selects 6e9.  A smaller
+ *              value only adds groups (more launches), never changes results.
+ *   eig_group_bytes  device memory for the shifted Neumann factors of one
+ *              group of subdomains in the GenEO eigensolver; the subdomains
+ *              are processed in consecutive groups that fit it.  <= 0 selects
+ *              4e10.  The random start vectors of the subspace iteration are
+ *              drawn per group, so another grouping changes the eigenvectors
+ *              within the eigensolver's convergence, not the solution of a
+ *              converged solve beyond its tolerance. */
 typedef struct {
     int px, py, pz, overlap, nev, max_iter, precision, resid_period;
     double tol, sigma;
     int eig_iters;
+    double factor_ws_bytes, eig_group_bytes;
 } gl_opts;
 
 /* Results of one solve.  rel_resid_true = ||f - K u||_2 / ||f||_2 on the
@@ -191,7 +205,10 @@ int gl_stress(gl_ctx *ctx, const double *u, double *s33, double *t13, double *pe
  * differences:
  *   - u (N entries), s33 and t13 (n_elem each) and peak_s33 (one double, may
  *     be NULL) must be device memory of the context's device, allocated by
- *     the caller; anything else is rejected with GL_ERR_INVALID_ARG;
+ *     the caller; anything else, and a buffer whose device allocation ends
+ *     before the entries the call touches (checked with cuMemGetAddressRange:
+ *     a short view into a larger allocation is not caught), is rejected with
+ *     GL_ERR_INVALID_ARG before any work is queued;
  *   - it calls no cudaMalloc, cudaFree or allocating library routine: the
  *     partial maxima of the resin peak live in a fixed array of 16,384
  *     doubles (128 KB) inside the library, which every GPU that loads the
@@ -200,7 +217,11 @@ int gl_stress(gl_ctx *ctx, const double *u, double *s33, double *t13, double *pe
  *   - the work is queued on the context's stream and the call returns without
  *     waiting for it;
  *   - the first call on a device looks up the array's device address and
- *     caches it; make that first call before any stream capture begins;
+ *     caches it.  With lazy module loading (the CUDA default) that first call
+ *     is also when the driver loads the library's module, and with it the
+ *     128 KB array, onto that device; make the first call before any stream
+ *     capture begins and before the caller's device memory is committed;
+ *     later calls allocate nothing;
  *   - all calls on a device share the one array, which keeps the last call's
  *     contents.  Each call writes every slot it reads before reading it, so
  *     nothing has to be cleared between calls, but calls whose work overlaps
@@ -304,6 +325,9 @@ typedef struct {
     int64_t factor_nonzeros;             /* entries of the lower-triangular factors
                                             (sum over fronts of p(p+1)/2 + p q):
                                             what the two sweeps read and multiply */
+    int factor_groups;                   /* subdomain groups of the local factorisation */
+    int eig_groups;                      /* subdomain groups of the GenEO eigensolver */
+    int max_level_fronts;                /* fronts of the most populated dissection level */
 } gl_profile_data;
 int gl_profile(gl_ctx *ctx, int enable);
 int gl_profile_read(gl_ctx *ctx, gl_profile_data *out);

@@ -478,7 +478,7 @@ void numeric_factor(FactorPlan &P, const double *C, const double *geo, const dou
         GL_CUDA(cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
     });
     const int nlev = (int)P.levels.size();
-    const int64_t budget = (int64_t)(6e9 / sizeof(T));   // entries per workspace buffer
+    const int64_t budget = (int64_t)(P.ws_budget_bytes / sizeof(T));   // entries per workspace buffer
     std::vector<int> depth_of(P.fr.size());
     for (int d = 0; d < nlev; ++d)
         for (int g : P.levels[d].fronts) depth_of[g] = d;
@@ -494,7 +494,9 @@ void numeric_factor(FactorPlan &P, const double *C, const double *geo, const dou
     DBuf<FrontDesc> d_fr;
     DBuf<T> ws[2];
     int j0 = 0;
+    P.last_groups = 0;
     while (j0 < P.n_sub) {
+        ++P.last_groups;
         // grow the group while every level's total stays within the budget
         std::vector<int64_t> tot(nlev, 0);
         int j1 = j0;

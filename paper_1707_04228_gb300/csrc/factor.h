@@ -37,6 +37,8 @@ struct FactorPlan {
     int64_t nnz = 0;                         // lower-triangle entries: sum p(p+1)/2 + p q
     int64_t ws_max = 0;
     int max_f = 0;
+    double ws_budget_bytes = 6e9;            // numeric_factor: workspace per buffer (subdomain groups fit it)
+    int last_groups = 0;                     // groups the last numeric_factor used
     // device
     DBuf<FrontDesc> d_fr;
     DBuf<int> d_rows, d_rel, d_pair_elem;

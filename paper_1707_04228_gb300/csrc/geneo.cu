@@ -468,6 +468,22 @@ void seg_check(SegScalars S, int n, double tol, int max_iter, int *n_active, cud
     GL_CUDA(cudaGetLastError());
 }
 
+__global__ void k_seg_confirm(SegScalars S, int n, double tol2, int max_iter, int *n_active) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || S.active[i] || !(S.ff[i] > 0.0) || S.iters[i] >= max_iter) return;
+    const double rr = S.rr[i];
+    if (rr > tol2 * S.ff[i] && rr < INFINITY) {
+        S.active[i] = 1;
+        atomicAdd(n_active, 1);
+    }
+}
+
+void seg_confirm(SegScalars S, int n, double tol, int max_iter, int *n_active, cudaStream_t s) {
+    GL_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), s));
+    k_seg_confirm<<<(n + 127) / 128, 128, 0, s>>>(S, n, tol * tol, max_iter, n_active);
+    GL_CUDA(cudaGetLastError());
+}
+
 void cg_update_p(double *p, const double *z, int64_t n, CGScalars *S, cudaStream_t s) {
     k_update_p<<<RED_BLOCKS, 256, 0, s>>>(p, z, n, S);
     k_finish_p<<<1, 1, 0, s>>>(S);

@@ -70,6 +70,10 @@ void seg_update_xr(double *x, double *r, const double *p, const double *q, const
 void seg_update_p(double *p, const double *z, const PartDesc *parts, int n, SegScalars S, cudaStream_t s);
 // for active parts: iters_i += 1, deactivate when rr_i <= tol^2 ff_i or iters_i >= max_iter; *n_active = count
 void seg_check(SegScalars S, int n, double tol, int max_iter, int *n_active, cudaStream_t s);
+// with rr_i the FP64 true residual of every part: reactivate the inactive parts that stopped below
+// max_iter on a recurrence residual whose true residual misses tol (rr_i > tol^2 ff_i, finite);
+// *n_active = how many were reactivated
+void seg_confirm(SegScalars S, int n, double tol, int max_iter, int *n_active, cudaStream_t s);
 
 // ---------------------------------------------------------------- PCG vector kernels
 struct CGScalars {

@@ -155,6 +155,9 @@ void launch_stress(const MeshHost &m, const double *X, const double *C, const do
                    const double *u, double *s33, double *t13, cudaStream_t s);
 void launch_failure(const MeshHost &m, const double *X, const double *C, const double *psi_x, const uint8_t *resin,
                     const double *u, double s33a, double s13a, double *F, unsigned long long *best, cudaStream_t s);
+// Fails with GL_ERR_INVALID_ARG unless [p, p + bytes) lies inside one device
+// allocation (cuMemGetAddressRange; no allocation is made).
+void require_device_span(const void *p, size_t bytes, const char *what);
 // Stress recovery into caller device buffers with the resin peak reduced
 // through a fixed file-scope device scratch (no device allocation).
 void stress_noalloc(const MeshHost &m, int device, const double *X, const double *C, const double *psi_x,

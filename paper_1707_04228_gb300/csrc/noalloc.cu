@@ -78,7 +78,40 @@ __global__ void __launch_bounds__(1024) k_peak_final(const double *__restrict__ 
     if (threadIdx.x == 0) *out = red[0];
 }
 
+// cuMemGetAddressRange of the driver API, reached through the runtime (the
+// library links no driver library), looked up once.
+using AddressRangeFn = int (*)(unsigned long long *base, size_t *size, unsigned long long ptr);
+
+AddressRangeFn address_range_fn() {
+    static std::once_flag once;
+    static AddressRangeFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<AddressRangeFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
 }  // namespace
+
+void require_device_span(const void *p, size_t bytes, const char *what) {
+    AddressRangeFn fn = address_range_fn();
+    if (!fn) fail(GL_ERR_CUDA, "cuMemGetAddressRange is not available from the driver");
+    unsigned long long base = 0;
+    size_t size = 0;
+    const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+    if (fn(&base, &size, a) != 0)
+        fail(GL_ERR_INVALID_ARG, std::string(what) + ": not inside a device allocation");
+    if (a < base || a - base > size || size - (a - base) < bytes)
+        fail(GL_ERR_INVALID_ARG, std::string(what) + ": the device allocation ends " +
+                                     std::to_string(size - (a - base)) + " bytes after it, the call needs " +
+                                     std::to_string(bytes));
+}
 
 void stress_noalloc(const MeshHost &m, int device, const double *X, const double *C, const double *psi_x,
                     const uint8_t *resin, const double *u, double *s33, double *t13, double *peak, cudaStream_t s) {

@@ -212,16 +212,18 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
     const int iters = o.eig_iters > 0 ? o.eig_iters : 100;
     // Groups of subdomains: factor of A^N + sigma Xi A^N Xi and block subspace
     // iteration for the largest mu of B p = mu M p, one group at a time.
-    const int64_t budget = (int64_t)(40e9 / sizeof(double));   // factor entries per group
+    const int64_t budget = (int64_t)((o.eig_group_bytes > 0 ? o.eig_group_bytes : 4e10) / sizeof(double));
     int j0 = 0, max_its = 0;
     while (j0 < nsub) {
         int j1 = j0;
         int64_t acc = 0;
         while (j1 < nsub && (j1 == j0 || acc + syms[j1].l_size <= budget)) acc += syms[j1++].l_size;
         const int ng = j1 - j0;
+        ++out.n_groups;
         std::vector<SubSymbolic> gs(syms.begin() + j0, syms.begin() + j1);
         FactorPlan PG;
         build_plan(gs, PG, s);
+        PG.ws_budget_bytes = PD.ws_budget_bytes;
         gs.clear();
         const int64_t goff = PN.vec_off[j0], gl = PG.n_local;
         DBuf<double> LN;

@@ -45,6 +45,7 @@ void problem_local_elems(const Problem &P, int s0, int s1, const FactorPlan &pla
 // the per-part coarse matrices K_0 = Z^T K Z (block diagonal over parts).
 struct Coarse {
     int nev = 0, n0 = 0, eig_iters = 0;
+    int n_groups = 0;              // subdomain groups of the eigensolver
     int n_dropped = 0;             // coarse columns left out as linearly dependent (all parts)
     std::vector<int> part_dropped;  // the same per part
     FactorPlan PN;

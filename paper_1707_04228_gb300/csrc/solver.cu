@@ -366,6 +366,7 @@ void setup(gl_ctx *c, const gl_opts &o) {
         problem_symbolic(P, false, LEAF_NODES, syms);
         build_plan(syms, c->PD, s);
     }
+    c->PD.ws_budget_bytes = c->opts.factor_ws_bytes > 0 ? c->opts.factor_ws_bytes : 6e9;
     stamp(c, "Dirichlet symbolic");
     if (std::getenv("GL_VERBOSE")) {
         // per dissection level: fronts, factor nonzeros the sweeps touch, the largest front
@@ -485,14 +486,33 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info, bool homogeneou
                 break;
             }
             rel = std::sqrt(rr / ff);
-            // stop on the recurrence residual; the FP64 true residual is reported after the loop
-            // (on these laminates its rounding floor lies near 1e-10 * ||K|| ||x|| / ||f||)
-            if (rel <= c->opts.tol) break;
+            // FP64: stop on the recurrence residual; the FP64 true residual is reported after the
+            // loop (on these laminates its rounding floor lies near 1e-10 * ||K|| ||x|| / ||f||).
+            // Mixed: the FP32 preconditioner lets the recurrence drift from the true residual, so
+            // a passing recurrence is confirmed on r = fe - K x in FP64; if that misses tol, r
+            // is replaced by it and the iteration goes on.
+            bool replaced = false;
+            if (rel <= c->opts.tol) {
+                if (!mixed) break;
+                apply_K(c, c->x.p, c->q.p);
+                set_entries(c->q.p, c->d_dir_dof.p, nd, nullptr, s);
+                sub(c->r.p, c->fe.p, c->q.p, N, s);
+                dot(c->r.p, c->r.p, N, c->partials.p, &S->rr, s);
+                g_launches += nds + 3;
+                const double rt = read_scalar(c, &S->rr);
+                if (!std::isfinite(rt)) {
+                    status = GL_ERR_NAN;
+                    break;
+                }
+                rel = std::sqrt(rt / ff);
+                if (rel <= c->opts.tol) break;
+                replaced = true;
+            }
             if (it == c->opts.max_iter) {
                 status = GL_ERR_NOT_CONVERGED;
                 break;
             }
-            if (mixed && it % c->opts.resid_period == 0) {
+            if (mixed && !replaced && it % c->opts.resid_period == 0) {
                 // residual replacement: r = fe - K x in FP64
                 apply_K(c, c->x.p, c->q.p);
                 set_entries(c->q.p, c->d_dir_dof.p, nd, nullptr, s);
@@ -791,6 +811,7 @@ void batch_setup(gl_batch *b, const gl_opts &o) {
         std::vector<SubSymbolic> syms;
         problem_symbolic(P, false, LEAF_NODES, syms);
         build_plan(syms, b->PD, s);
+        b->PD.ws_budget_bytes = b->opts.factor_ws_bytes > 0 ? b->opts.factor_ws_bytes : 6e9;
     }
     if (b->opts.precision == GL_PREC_MIXED) {
         b->LD64.release();
@@ -894,7 +915,25 @@ void batch_solve(gl_batch *b, double *const *u, gl_info *infos) {
         g_launches += per_iter;
         GL_CUDA(cudaMemcpyAsync(b->h_active, b->ints.p + 2 * n, sizeof(int), cudaMemcpyDeviceToHost, s));
         GL_CUDA(cudaStreamSynchronize(s));
-        if (*b->h_active == 0) break;
+        if (*b->h_active == 0) {
+            if (b->opts.precision != GL_PREC_MIXED) break;
+            // mixed: every laminate stopped on its recurrence residual; confirm on the FP64 true
+            // residual r = fe - K x and restart (z = M r, p = z) those that miss tol
+            batch_ku(b, b->x.p, b->q.p);
+            set_entries(b->q.p, b->d_dir.p, b->ndir, nullptr, s);
+            sub(b->r.p, b->fe.p, b->q.p, N, s);
+            seg_dot(b->r.p, b->r.p, b->d_parts.p, n, b->partials.p, S.rr, s);
+            seg_confirm(S, n, b->opts.tol, b->opts.max_iter, b->ints.p + 2 * n, s);
+            g_launches += 4 + (b->ndir ? 1 : 0);
+            GL_CUDA(cudaMemcpyAsync(b->h_active, b->ints.p + 2 * n, sizeof(int), cudaMemcpyDeviceToHost, s));
+            GL_CUDA(cudaStreamSynchronize(s));
+            if (*b->h_active == 0) break;
+            batch_precond(b, b->r.p, b->z.p);
+            seg_dot(b->r.p, b->z.p, b->d_parts.p, n, b->partials.p, S.rho, s);
+            GL_CUDA(cudaMemcpyAsync(b->p.p, b->z.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            g_launches += 2;
+            continue;
+        }
         if (b->opts.precision == GL_PREC_MIXED && it % period == 0) {
             // FP64 residual replacement r = fe - K x (frozen laminates keep their r: x is unchanged)
             batch_ku(b, b->x.p, b->q.p);
@@ -927,8 +966,10 @@ void batch_solve(gl_batch *b, double *const *u, gl_info *infos) {
         const double ff = hs[4 * n + i], rr = hs[3 * n + i];
         const int iters = hi[n + i];
         int st = GL_OK;
-        if (!std::isfinite(rr)) st = GL_ERR_NAN;
-        else if (ff > 0 && rr > b->opts.tol * b->opts.tol * ff) st = GL_ERR_NOT_CONVERGED;
+        // mixed: accepted on the FP64 true residual; FP64: on the recurrence residual
+        const double racc = b->opts.precision == GL_PREC_MIXED ? hrt[i] : rr;
+        if (!std::isfinite(rr) || !std::isfinite(racc)) st = GL_ERR_NAN;
+        else if (ff > 0 && racc > b->opts.tol * b->opts.tol * ff) st = GL_ERR_NOT_CONVERGED;
         if (st != GL_OK) worst = st;
         if (u[i]) from_device(u[i], b->x.p + b->parts[i].dof_off, b->parts[i].n_dof, s);
         if (infos) {
@@ -1229,8 +1270,18 @@ int gl_stress_noalloc(gl_ctx *c, const double *u, double *s33, double *t13, doub
             }
             return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == c->device;
         };
-        GL_REQUIRE(on_ctx_device(u) && on_ctx_device(s33) && on_ctx_device(t13) && (!peak || on_ctx_device(peak)),
-                   "gl_stress_noalloc: every buffer must be device memory of the context's device");
+        // each buffer in turn: device memory of the context's device, long enough for what the
+        // kernels touch (N doubles of u read; n_elem doubles of s33, t13 and one of peak written);
+        // all checks come before the first launch
+        auto check = [&](const void *p, size_t bytes, const char *name) {
+            GL_REQUIRE(on_ctx_device(p), std::string("gl_stress_noalloc: ") + name +
+                                             " must be device memory of the context's device");
+            require_device_span(p, bytes, (std::string("gl_stress_noalloc: ") + name).c_str());
+        };
+        check(u, c->m.n_dof * sizeof(double), "u");
+        check(s33, c->m.n_elem * sizeof(double), "s33");
+        check(t13, c->m.n_elem * sizeof(double), "t13");
+        if (peak) check(peak, sizeof(double), "peak_s33");
         stress_noalloc(c->m, c->device, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_resin.p, u, s33, t13, peak, c->stream);
         g_launches += 1 + (peak ? 2 : 0);
     });
@@ -1398,8 +1449,13 @@ int gl_profile_read(gl_ctx *c, gl_profile_data *out) {
         out->n_sub = (int)c->prob.boxes.size();
         out->n_coarse_dim = c->co.n0;
         out->factor_levels = 0;
-        for (auto &L : c->PD.levels)
+        out->max_level_fronts = 0;
+        for (auto &L : c->PD.levels) {
             if (!L.fronts.empty()) ++out->factor_levels;
+            out->max_level_fronts = std::max(out->max_level_fronts, (int)L.fronts.size());
+        }
+        out->factor_groups = c->PD.last_groups;
+        out->eig_groups = c->co.n_groups;
     });
 }
 

@@ -42,7 +42,8 @@ class gl_mesh(C.Structure):
 class gl_opts(C.Structure):
     _fields_ = [("px", C.c_int), ("py", C.c_int), ("pz", C.c_int), ("overlap", C.c_int), ("nev", C.c_int),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("resid_period", C.c_int),
-                ("tol", C.c_double), ("sigma", C.c_double), ("eig_iters", C.c_int)]
+                ("tol", C.c_double), ("sigma", C.c_double), ("eig_iters", C.c_int),
+                ("factor_ws_bytes", C.c_double), ("eig_group_bytes", C.c_double)]
 
 
 class gl_info(C.Structure):
@@ -60,7 +61,8 @@ class gl_profile_data(C.Structure):
                 ("n_ku", C.c_int64), ("n_local", C.c_int64), ("n_coarse", C.c_int64),
                 ("factor_entries", C.c_int64), ("local_dofs", C.c_int64), ("factor_bytes_per_entry", C.c_int),
                 ("factor_levels", C.c_int), ("n_elem", C.c_int64), ("n_dof", C.c_int64), ("n_sub", C.c_int),
-                ("n_coarse_dim", C.c_int), ("factor_nonzeros", C.c_int64)]
+                ("n_coarse_dim", C.c_int), ("factor_nonzeros", C.c_int64), ("factor_groups", C.c_int),
+                ("eig_groups", C.c_int), ("max_level_fronts", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -209,9 +211,10 @@ class Solver:
         _check(self.lib, self.lib.gl_set_traction(self.ctx, int(face), _ptr(tv)))
 
     def setup(self, px, py, pz, overlap=1, nev=8, tol=1e-10, max_iter=2000, precision=GL_PREC_FP64,
-              resid_period=50, sigma=0.0, eig_iters=0):
+              resid_period=50, sigma=0.0, eig_iters=0, factor_ws_bytes=0.0, eig_group_bytes=0.0):
         o = gl_opts(px=px, py=py, pz=pz, overlap=overlap, nev=nev, max_iter=max_iter, precision=precision,
-                    resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters)
+                    resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters,
+                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes)
         _check(self.lib, self.lib.gl_setup(self.ctx, C.byref(o)))
 
     @classmethod
@@ -267,9 +270,17 @@ class Solver:
         device buffers (torch tensors or raw device addresses); nothing is
         allocated and the call returns before the work on the context's stream
         is done."""
-        def dptr(a):
-            return C.c_void_p(a) if isinstance(a, int) else _ptr(a)
-        _check(self.lib, self.lib.gl_stress_noalloc(self.ctx, dptr(u), dptr(s33), dptr(t13), dptr(peak)))
+        def dptr(a, n, name):
+            if a is None or isinstance(a, int):
+                return None if a is None else C.c_void_p(a)
+            if hasattr(a, "data_ptr"):
+                import torch
+                if a.dtype != torch.float64 or not a.is_cuda or a.numel() < n:
+                    raise ValueError(f"{name}: needs a CUDA float64 tensor of at least {n} entries")
+            return _ptr(a)
+        ne = self.n_elem
+        _check(self.lib, self.lib.gl_stress_noalloc(self.ctx, dptr(u, self.n_dof, "u"), dptr(s33, ne, "s33"),
+                                                    dptr(t13, ne, "t13"), dptr(peak, 1, "peak")))
 
     def apply_K(self, x, out=None):
         out = np.empty(self.n_dof) if out is None else out
@@ -352,9 +363,10 @@ class Batch:
         _check(self.lib, self.lib.gl_batch_create(C.byref(self.b), len(self.solvers), C.cast(arr, C.c_void_p), sp))
 
     def setup(self, px=0, py=0, overlap=1, nev=8, tol=1e-10, max_iter=2000, precision=GL_PREC_FP64,
-              resid_period=50, sigma=0.0, eig_iters=0):
+              resid_period=50, sigma=0.0, eig_iters=0, factor_ws_bytes=0.0, eig_group_bytes=0.0):
         o = gl_opts(px=px, py=py, pz=1, overlap=overlap, nev=nev, max_iter=max_iter, precision=precision,
-                    resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters)
+                    resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters,
+                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes)
         _check(self.lib, self.lib.gl_batch_setup(self.b, C.byref(o)))
 
     def grid(self):

@@ -407,6 +407,135 @@ def test_curved_map_geometry():
     assert np.allclose(X[:, :, -1, 0], lam.limb_L + rn[:, None])
 
 
+# --------------------------------------------------------------------------- orientation conventions
+#
+# The material axes and the stress frame are fixed by the geometry: a fibre
+# runs along the ply (the tangent of the mapped mesh), a ply angle turns it
+# about the outward normal r from s toward the width axis l (the usual
+# laminate convention; the paper gives stacks such as [0/90/+45/-45]s without
+# fixing the sign, Section 2.2), and sigma_33 is the normal stress on the
+# through-thickness direction of the curved laminate (Section 2.2 notation,
+# Section 3 map).  These pins measure the stiffest direction of C_e and the
+# frame from node positions, not from the oracle's rotation matrices.
+
+
+def _stiffness_along(C, n):
+    """Directional stiffness e^T C e of the uniaxial strain n (x) n (Voigt, engineering shears), rows of n."""
+    n = np.atleast_2d(n)
+    e = np.stack([n[:, 0] ** 2, n[:, 1] ** 2, n[:, 2] ** 2, 2 * n[:, 1] * n[:, 2], 2 * n[:, 0] * n[:, 2],
+                  2 * n[:, 0] * n[:, 1]], axis=1)
+    return np.einsum("ni,ij,nj->n", e, C, e)
+
+
+def _stiffest_direction(C):
+    """Unit n maximising the quartic e(n)^T C e(n): best of 20,000 Fibonacci-sphere
+    samples, refined by the shifted symmetric higher-order power method
+    (n <- normalise(grad/4 + a n), monotone for a shift a above the quartic's
+    curvature bound)."""
+    k = np.arange(20000) + 0.5
+    z = 1.0 - 2.0 * k / k.size
+    rho = np.sqrt(1.0 - z * z)
+    ph = math.pi * (1.0 + math.sqrt(5.0)) * k
+    pts = np.stack([rho * np.cos(ph), rho * np.sin(ph), z], axis=1)
+    n = pts[np.argmax(_stiffness_along(C, pts))]
+    a = 4.0 * np.abs(C).sum()
+    for _ in range(5000):
+        e = np.array([n[0] ** 2, n[1] ** 2, n[2] ** 2, 2 * n[1] * n[2], 2 * n[0] * n[2], 2 * n[0] * n[1]])
+        D = np.array([[2 * n[0], 0, 0], [0, 2 * n[1], 0], [0, 0, 2 * n[2]], [0, 2 * n[2], 2 * n[1]],
+                      [2 * n[2], 0, 2 * n[0]], [2 * n[1], 2 * n[0], 0]])
+        g = 2.0 * D.T @ (C @ e)
+        m = g / 4.0 + a * n
+        m /= np.linalg.norm(m)
+        if np.linalg.norm(m - n) < 1e-15:
+            n = m
+            break
+        n = m
+    return n
+
+
+def _angle(a, b):
+    c = abs(float(np.dot(a, b))) / (np.linalg.norm(a) * np.linalg.norm(b))
+    return math.acos(min(1.0, c))
+
+
+def test_fibre_follows_the_arc_tangent_and_ply_angle():
+    """On a curved corner without misalignment, the stiffest direction of every
+    ply element's C_e is cos(phi) t + sin(phi) e_l, with t the unit tangent of
+    the mapped mesh at the element centre taken from two node positions (the
+    chord between the centres of the element's -s and +s faces, parallel to
+    the arc's tangent at the centre and exact on the limbs)."""
+    lam = inputs.corner_mini(n_arc=6, n_limb=1, n_width=2, nel_layer=1, angles=(0, 45, -45, 90), amp_deg=0.0)
+    mesh = fem.Mesh(lam)
+    assert np.all(mesh.theta == 0.0)
+    phi = np.radians(np.asarray(lam.layer_angle_deg, dtype=np.float64))[mesh.layer_of_elem]
+    psi_seen = set()
+    checked = 0
+    for e in range(0, mesh.n_elem, 3):
+        if mesh.is_resin[e]:
+            continue
+        t = mesh.X[mesh.conn[e][14]] - mesh.X[mesh.conn[e][12]]
+        t /= np.linalg.norm(t)
+        fibre = math.cos(phi[e]) * t + math.sin(phi[e]) * np.array([0.0, 1.0, 0.0])
+        n = _stiffest_direction(mesh.C[e])
+        assert _angle(n, fibre) <= 1e-6, (e, n, fibre)
+        psi_seen.add(round(float(mesh.psi[e]), 6))
+        checked += 1
+    assert checked > 20 and len(psi_seen) >= 5       # limbs and several arc positions
+
+
+def test_positive_ply_angle_turns_the_fibre_toward_the_width_axis():
+    """Flat plate: a +45 ply is stiffest along (1, 1, 0)/sqrt 2, a -45 ply along
+    (1, -1, 0)/sqrt 2, a 90 ply along the width axis, a 0 ply along s."""
+    lam = block(1, 1, [(1, 0.25, 0, 45.0), (1, 0.25, 0, -45.0), (1, 0.25, 0, 90.0), (1, 0.25, 0, 0.0)])
+    mesh = fem.Mesh(lam)
+    r2 = 1.0 / math.sqrt(2.0)
+    want = [np.array([r2, r2, 0.0]), np.array([r2, -r2, 0.0]), np.array([0.0, 1.0, 0.0]),
+            np.array([1.0, 0.0, 0.0])]
+    for e, w in enumerate(want):
+        assert _angle(_stiffest_direction(mesh.C[e]), w) <= 1e-6
+    # misalignment tilts a 0 ply's fibre in the s-r plane: theta > 0 turns it from +s toward -r
+    lam.theta = np.full((4, 1, 1), 0.2)
+    mesh = fem.Mesh(lam)
+    n = _stiffest_direction(mesh.C[3])
+    assert _angle(n, np.array([math.cos(0.2), 0.0, -math.sin(0.2)])) <= 1e-6
+
+
+def test_curved_stress_frame_from_positions():
+    """Homogeneous isotropic corner under a linear displacement u = A x: the
+    stress is the same tensor S everywhere (Q2 holds linear fields exactly),
+    and sigma_33, tau_13 returned per element must equal n_r^T S n_r and
+    n_s^T S n_r with n_r the outward radial unit vector computed from the
+    element centre's position (x_c - L, 0, z_c) on the arc, (0, 0, 1) on limb 1
+    and (1, 0, 0) on limb 2 of the 90-degree corner, and n_s = n_l x n_r the
+    direction of increasing s."""
+    lam = inputs.corner_mini(n_arc=6, n_limb=1, n_width=2, nel_layer=1, angles=(0, 90), amp_deg=0.0)
+    lam.layer_mat = [1] * len(lam.layer_mat)            # resin everywhere: C uniform
+    mesh = fem.Mesh(lam)
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((3, 3)) * 1e-3
+    u = (mesh.X @ A.T).ravel()
+    E, nu = inputs.RESIN_T1["E"], inputs.RESIN_T1["nu"]
+    eps = 0.5 * (A + A.T)
+    S = E / (1 + nu) * (eps + nu / (1 - 2 * nu) * np.trace(eps) * np.eye(3))
+    s33, t13 = fem.stress_slr(mesh, u)
+    t = fem.q2_node_params(lam.sv)
+    for e in range(mesh.n_elem):
+        xc = mesh.X[mesh.conn[e][13]]
+        ex = mesh.eijk[e, 0]
+        tc = t[2 * ex + 1]
+        if tc < 0.0:
+            nr = np.array([0.0, 0.0, 1.0])
+        elif tc > 1.0:
+            nr = np.array([1.0, 0.0, 0.0])
+        else:
+            nr = np.array([xc[0] - lam.limb_L, 0.0, xc[2]])
+            nr /= np.linalg.norm(nr)
+        ns = np.cross(np.array([0.0, 1.0, 0.0]), nr)
+        assert abs(s33[e] - nr @ S @ nr) <= 1e-10 * np.abs(S).max()
+        assert abs(t13[e] - ns @ S @ nr) <= 1e-10 * np.abs(S).max()
+    assert np.ptp(s33) > 0.1 * np.abs(S).max()         # the frame really turns
+
+
 def test_direct_solvers_agree_with_dense_cholesky():
     lam = inputs.corner_mini(n_arc=3, n_limb=1, n_width=2, nel_layer=1, nsub=(2, 1, 1), nev=6)
     mesh = fem.Mesh(lam)

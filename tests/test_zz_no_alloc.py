@@ -80,3 +80,49 @@ def test_without_peak_and_rejections(solver):
     with pytest.raises(lib.GLError) as e:
         s.stress_noalloc(u, s33, t13)
     assert e.value.code == -1   # GL_ERR_INVALID_ARG
+    # the binding refuses tensors of the wrong type or length before calling the library
+    with pytest.raises(ValueError):
+        s.stress_noalloc(ud.float(), s33, t13)
+    with pytest.raises(ValueError):
+        s.stress_noalloc(ud, s33[:-1], t13)
+    with pytest.raises(ValueError):
+        s.stress_noalloc(ud, s33, t13, torch.empty(0, dtype=torch.float64, device="cuda"))
+
+
+def test_short_device_allocation_is_rejected_before_any_launch(solver):
+    """A raw device address 8 bytes before the end of its allocation cannot
+    hold the N entries of u: the library rejects it from the allocation's
+    extent.  s33 is a host array here, so the call stops at the buffer checks
+    whatever happens: it names u only if the extent check caught it."""
+    import torch
+    from paper_1707_04228_gb300 import lib
+    s = solver
+    ud = torch.zeros(s.n_dof, dtype=torch.float64, device="cuda")
+    seg = [g for g in torch.cuda.memory_snapshot()
+           if g["address"] <= ud.data_ptr() < g["address"] + g["total_size"]]
+    assert len(seg) == 1
+    end = seg[0]["address"] + seg[0]["total_size"]
+    host = np.empty(s.n_elem)
+    with pytest.raises(lib.GLError) as e:
+        s.stress_noalloc(int(end - 8), host, host)
+    assert e.value.code == -1 and "u: the device allocation ends 8 bytes" in str(e.value)
+
+
+def test_calls_after_the_first_allocate_no_device_memory(solver):
+    """The point of the entry point: once the first call on the device has run
+    (it may load the library's module and its fixed array), further calls
+    leave the device's free memory exactly where it was."""
+    import torch
+    s = solver
+    ud = torch.from_numpy(inputs.random_vector(s.n_dof, 34) * 1e-3).cuda()
+    s33 = torch.empty(s.n_elem, dtype=torch.float64, device="cuda")
+    t13 = torch.empty_like(s33)
+    peak = torch.empty(1, dtype=torch.float64, device="cuda")
+    s.stress_noalloc(ud, s33, t13, peak)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        s.stress_noalloc(ud, s33, t13, peak)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
