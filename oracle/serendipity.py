@@ -136,3 +136,59 @@ def solve_dirichlet(mesh, K, f, dir_dof, dir_val):
     rhs = f[free] - K[free][:, dir_dof] @ np.asarray(dir_val)
     u[free] = spla.spsolve(K[free][:, free].tocsc(), rhs)
     return u
+
+
+def traction_load20(mesh, face, t):
+    """Consistent nodal loads of a uniform traction t (MPa) on one box face of
+    a serendipity mesh: f_a = int_face N_a t dA by the 3x3 Gauss rule on every
+    element face lying on `face` (faces numbered as in oracle.fem: 0 -s, 1 +s,
+    2 -l, 3 +l, 4 -r, 5 +r).  On the face the 20 shape functions reduce to the
+    8-node serendipity quadrilateral (the others vanish there)."""
+    q2 = mesh.q2
+    axis, side = fem.FACE_AXIS[face]
+    n_e = (q2.nx, q2.ny, q2.nz)[axis]
+    fix = -1.0 if side == 0 else 1.0
+    e_fix = 0 if side == 0 else n_e - 1
+    g, w = fem.gauss3()
+    others = [d for d in range(3) if d != axis]
+    tv = np.asarray(t, dtype=np.float64)
+    f = np.zeros(mesh.n_dof)
+    for e in np.nonzero(q2.eijk[:, axis] == e_fix)[0]:
+        Xe = mesh.X[mesh.conn[e]]
+        d = (3 * mesh.conn[e][:, None] + np.arange(3)[None, :]).ravel()
+        for i, a in enumerate(g):
+            for j, b in enumerate(g):
+                p = [0.0, 0.0, 0.0]
+                p[axis] = fix
+                p[others[0]] = a
+                p[others[1]] = b
+                N, dN = shape20(*p)
+                J = Xe.T @ dN
+                dA = np.linalg.norm(np.cross(J[:, others[0]], J[:, others[1]]))
+                f[d] += w[i] * w[j] * dA * np.kron(N, tv)
+    return f
+
+
+def stress_slr20(mesh, u):
+    """sigma_33 = sigma_rr and tau_13 = tau_rs at every element centre of a
+    serendipity mesh (u in its own numbering): sigma = C_e eps(u) with the
+    20-node gradients at xi = 0 and the 20-node geometry map, rotated into the
+    local (s, l, r) frame as in oracle.fem.stress_slr."""
+    _, dN = shape20(0.0, 0.0, 0.0)
+    q2 = mesh.q2
+    s33 = np.zeros(mesh.n_elem)
+    t13 = np.zeros(mesh.n_elem)
+    for e in range(mesh.n_elem):
+        Xe = mesh.X[mesh.conn[e]]
+        J = Xe.T @ dN
+        dNdx = dN @ np.linalg.inv(J)
+        d = (3 * mesh.conn[e][:, None] + np.arange(3)[None, :]).ravel()
+        sv = mesh.C[e] @ (strain_B20(dNdx) @ u[d])
+        S = np.zeros((3, 3))
+        for I, (i, j) in enumerate(fem.VOIGT):
+            S[i, j] = S[j, i] = sv[I]
+        Rf = fem.rot_width(q2.psi[e])
+        Sl = Rf.T @ S @ Rf
+        s33[e] = Sl[2, 2]
+        t13[e] = Sl[0, 2]
+    return s33, t13
