@@ -46,7 +46,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PCG DOF-iterations/s at 1e-10 rel. residual; K*u HBM GB/s vs peak"
 UNIT = "DOF-iterations/s"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_FMA_PER_SM_CLK = 2        # nominal FP64 FMA rate per SM and clock of this part (context only)
+
+
+def fp64_peak(device):
+    """FP64 peak measured in this run by the library's FMA probe (no memory
+    traffic, 8 independent chains per thread, 8 blocks of 256 per SM), with the
+    SM clocks sampled meanwhile; the nominal rate n_SM x 2 FMA/clk x 2 flop x
+    max clock is reported beside it."""
+    from paper_1707_04228_gb300 import lib
+    with ClockSampler(device) as clk:
+        flops, n_sm, ms = lib.fp64_peak_probe(device, iters=8192, reps=40)
+    c = clk.summary()
+    mx = c["sm_max_mhz"] or 2070.0
+    return {"tflops": flops / 1e12, "n_sm": n_sm, "ms": ms, "clocks": c,
+            "nominal_tflops": n_sm * FP64_FMA_PER_SM_CLK * 2 * mx * 1e6 / 1e12}
 
 
 def peaks():
@@ -81,10 +95,14 @@ def workload(name):
         desc = ("paper_corner_120x60x77_q2: the 39-ply wrinkle-study geometry (R 22 mm, 10 mm limbs, 52 mm width, "
                 "0.24/0.015 mm plies/resin, sech^2 wrinkle of 0.62 mm), 13,559,865 DOF, 128 subdomains (32x4x1), "
                 "10 eigenvectors, mixed (FP32 local factors and sweeps), tol 1e-8")
-    elif name == "corner_small":
+    elif name in ("corner_small", "corner_small_mixed"):
         lam = inputs.curved_corner(n_arc=24, n_limb=4, n_width=8, nel_layer=1, name="curved_corner_small",
                                    nsub=(8, 2, 1), nev=10)
-        desc = "curved_corner_32x8x23_q2 (small dry-run case), 16 subdomains, 10 eigenvectors, FP64, tol 1e-10"
+        mixed = name == "corner_small_mixed"
+        lam.precision = 1 if mixed else 0
+        lam.tol = 1e-8 if mixed else 1e-10
+        desc = ("curved_corner_32x8x23_q2 (small dry-run case), 16 subdomains, 10 eigenvectors, "
+                + ("mixed, tol 1e-8" if mixed else "FP64, tol 1e-10"))
     else:
         raise SystemExit(f"unknown config {name}")
     return lam, desc
@@ -180,39 +198,74 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_batch(args):
+def shard_worklist(costs, world):
+    """Static split of independent laminates over `world` replicas: largest
+    first, each to the least loaded rank (ties to the lower rank).  Returns
+    one sorted index list per rank; every index appears exactly once."""
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += costs[i]
+    return [sorted(o) for o in out]
+
+
+def run_batch(args, rank=0, local_rank=0, world=1):
     """96 flat laminates of 40k-800k DOF solved together (one launch per phase,
     graph-replayed iterations, autotuned decompositions, FP64 CG with FP32
     local factors); value = sum of free DOFs x iterations over all laminates
-    per second of the batched solve."""
+    per second of the batched solve.  With N replicas the laminates are split
+    by shard_worklist (by DOF) and each rank solves its share as one batch; the
+    whole-job value is the sum of all ranks' work over the slowest rank's time."""
     import torch
     from paper_1707_04228_gb300 import inputs, lib
-    lams = inputs.batch_plates(count=args.count, nev=8)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    all_lams = inputs.batch_plates(count=args.count, nev=8)
+    mine = shard_worklist([l.n_dof for l in all_lams], world)[rank]
+    lams = [all_lams[i] for i in mine]
     t0 = time.perf_counter()
-    b = lib.Batch(lams)
+    b = lib.Batch(lams, device=local_rank)
     b.setup(px=0, py=0, nev=8, tol=1e-8, precision=lib.GL_PREC_MIXED, max_iter=3000)
     setup_s = time.perf_counter() - t0
-    outs = [torch.empty(l.n_dof, dtype=torch.float64, device="cuda") for l in lams]
+    outs = [torch.empty(l.n_dof, dtype=torch.float64, device=dev) for l in lams]
     for _ in range(args.warmup):
         _, infos = b.solve(outs)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     units, ms = 0, 0.0
-    for _ in range(args.steps):
-        t1 = time.perf_counter()
-        _, infos = b.solve(outs)
-        torch.cuda.synchronize()
-        ms += 1e3 * (time.perf_counter() - t1)
-        units += sum(i["n_free"] * i["iters"] for i in infos)
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            _, infos = b.solve(outs)
+            torch.cuda.synchronize()
+            ms += 1e3 * (time.perf_counter() - t1)
+            units += sum(i["n_free"] * i["iters"] for i in infos)
+    if world > 1:
+        dist.barrier()
+    t_max, units = aggregate_ranks(ms, units, world, dev)
     grid = b.grid().tolist()
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": f"batch of {len(lams)} flat laminates, {sum(l.n_dof for l in lams):,} DOF in "
-                                   f"total, autotuned in-plane grids, 8 eigenvectors, mixed, tol 1e-8"},
-            "setup_s": setup_s, "iters": [i["iters"] for i in infos],
-            "rel_resid_true_max": max(i["rel_resid_true"] for i in infos), "grids": grid}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        line = {"metric": METRIC, "value": units / (t_max / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / max(args.steps, 1),
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64+f32",
+                "data": "synthetic",
+                "config": {"workload": f"batch of {len(all_lams)} flat laminates, "
+                                       f"{sum(l.n_dof for l in all_lams):,} DOF in total, autotuned in-plane grids, "
+                                       f"8 eigenvectors, mixed, tol 1e-8",
+                           "parallelism": "replicas (laminates split by DOF)" if world > 1 else "single GPU"},
+                "setup_s": setup_s, "iters": [i["iters"] for i in infos],
+                "rel_resid_true_max": max(i["rel_resid_true"] for i in infos), "grids": grid,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
     b.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_adjoint(args):
@@ -220,8 +273,9 @@ def run_adjoint(args):
     resin elements of the arc, differentiated through torch.autograd with respect
     to every element's misalignment angle (one forward and one adjoint PCG solve
     per gradient).  value = free DOFs x (forward + adjoint iterations) per second;
-    gradient_s = the time of one gradient.  --fd N compares the N largest patch
-    components with central differences (h = 1e-6 rad) of the same solver."""
+    gradient_s = the time of one gradient.  --fd N compares N patch components
+    drawn with seed 4228 with central differences (h = 1e-6 rad), each
+    perturbed state reached by an increment solve from u(theta0)."""
     import torch
     from paper_1707_04228_gb300 import inputs, lib
     from paper_1707_04228_gb300.autograd import pnorm, stress_of_theta
@@ -260,17 +314,18 @@ def run_adjoint(args):
     gp = gfull[patch]
     fd = []
     if args.fd > 0:
-        for e in np.flatnonzero(patch)[np.argsort(-np.abs(gp))[:args.fd]]:
-            vals = []
-            for sgn in (1.0, -1.0):
-                th = theta0.clone()
-                th[int(e)] += sgn * 1e-6
-                with torch.no_grad():
-                    vals.append(pnorm(stress_of_theta(th, s, f), mask, 8).item())
-            d = (vals[0] - vals[1]) / 2e-6
+        # args.fd patch parameters drawn with seed 4228; J(theta0 +- h e_k) by increment solves from u(theta0)
+        from paper_1707_04228_gb300.autograd import theta_central_differences
+        elems = np.random.default_rng(4228).choice(np.flatnonzero(patch), args.fd, replace=False)
+        t_fd = time.perf_counter()
+        vals = theta_central_differences(s, lam.nx, lam.ny, theta0, elems, mask, 8, 1e-6, f)
+        fd_s = time.perf_counter() - t_fd
+        for e, d in zip(elems, vals):
             fd.append({"elem": int(e), "adjoint": float(gfull[e]), "fd": d,
                        "rel_diff": abs(d - gfull[e]) / abs(gfull[e])})
-        s.set_theta(theta0)
+        rd = [x["rel_diff"] for x in fd]
+        fd = {"n": len(fd), "h": 1e-6, "seed": 4228, "max_rel_diff": max(rd), "median_rel_diff": float(np.median(rd)),
+              "time_s": fd_s, "samples": fd}
     line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -312,13 +367,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count", type=int, default=96, help="laminates in --config batch")
     ap.add_argument("--fd", type=int, default=0, help="central-difference checks in --config adjoint")
+    ap.add_argument("--fp32-update", type=int, default=0, choices=[0, 1],
+                    help="mixed precision: trailing updates of the FP32 factors on the tensor cores (0) or the "
+                         "FP32 CUDA cores (1)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="after a mixed-precision run, solve the same laminate in FP64 and report the differences")
     args = ap.parse_args()
     rank, local_rank, world = dist_env()
     if args.config == "batch" and args.impl == "ours":
-        if rank == 0:
-            run_batch(args)
+        run_batch(args, rank, local_rank, world)
         return
     if args.config == "adjoint" and args.impl == "ours":
         if rank == 0:
@@ -349,7 +406,8 @@ def main():
     lam, desc = workload(args.config)
     t0 = time.perf_counter()
     prec = getattr(lam, "precision", 0)
-    s = lib.Solver.from_laminate(lam, device=local_rank, precision=prec, max_iter=5000)
+    s = lib.Solver.from_laminate(lam, device=local_rank, precision=prec, max_iter=5000,
+                                 fp32_update=args.fp32_update)
     setup_s = time.perf_counter() - t0
     N, NE = s.n_dof, s.n_elem
     dev = torch.device("cuda", local_rank)
@@ -363,6 +421,8 @@ def main():
         _, info = s.solve(f, out=u)
         s.stress(u, s33, t13)
     torch.cuda.synchronize()
+    probe = fp64_peak(local_rank)
+    FP64_PEAK_TFLOPS = probe["tflops"]
 
     def barrier():
         if world > 1:
@@ -414,7 +474,7 @@ def main():
     loc_flops = 4 * fe
     loc_ms = prof["ms_local"] / max(prof["n_local"], 1)
     ku_bytes = 16 * N + NE * (36 + 270) * 8                         # x in, y out, C_e and Gauss-point J^-1, w|J|
-    ku_flops = NE * 6318 * 2                                        # sum-factorised FMA count per element
+    ku_flops = NE * (2 * 5346 + 162)                                # collocation sum factorisation: FMA, MUL
     ku_ms = prof["ms_ku"] / max(prof["n_ku"], 1)
     per_iter = {"ku_ms": ku_ms, "local_ms": loc_ms, "coarse_ms": prof["ms_coarse"] / max(prof["n_coarse"], 1)}
     loc_tf = loc_flops / (loc_ms / 1e3) / 1e12
@@ -424,7 +484,8 @@ def main():
                 "frac": loc_tf / FP64_PEAK_TFLOPS, "traffic": None,
                 "kernel": "local forward/backward supernodal sweeps (all levels) + gather/scatter",
                 "hbm_gbs": loc_bytes / (loc_ms / 1e3) / 1e9, "hbm_frac": loc_bytes / (loc_ms / 1e3) / 1e9 / hbm,
-                "peak_note": f"FP64 ALU peak derived from 152 SMs x 2 FMA/clk x 2.07 GHz; HBM {hbm} GB/s {hbm_src}"}
+                "peak_note": f"FP64 peak measured in this run by the FMA probe ({probe['n_sm']} SMs, nominal "
+                             f"{probe['nominal_tflops']:.3f} TFLOP/s); HBM {hbm} GB/s {hbm_src}"}
     else:
         gbs = loc_bytes / (loc_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
@@ -468,9 +529,12 @@ def main():
                            f"{fe * bpe / 1e9:.1f} GB stream every iteration)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roof, "ku": ku, "per_iteration": per_iter, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk.summary(), "gpu_launches": launches, "setup_s": setup_s,
+                "clocks": clk.summary(), "fp64_probe": probe, "gpu_launches": launches, "setup_s": setup_s,
                 "iters_per_solve": iters / max(args.steps, 1), "rel_resid_true": info["rel_resid_true"],
                 "n_free": info["n_free"], "factor_nonzeros": fe, "n_coarse": info["n_coarse"]}
+        if prec == 1:
+            line["config"]["fp32_update"] = ("tensor cores (tcgen05 kind::tf32, 3xTF32 split, rank-128 panels)"
+                                             if args.fp32_update == 0 else "FP32 CUDA cores (rank-32)")
         if vs_fp64 is not None:
             line["vs_fp64"] = vs_fp64
         print(json.dumps(line), flush=True)

@@ -50,7 +50,7 @@ enum {
     GL_ERR_NOT_SPD = -4,        /* a Cholesky pivot was <= 0 (local or coarse factor) */
     GL_ERR_NOT_CONVERGED = -5,  /* max_iter reached; info and u still filled */
     GL_ERR_NAN = -6,            /* a NaN or Inf appeared in the iteration */
-    GL_ERR_TIMEOUT = -7,        /* a device-side wait gave up */
+    GL_ERR_TIMEOUT = -7,        /* a device-side wait gave up (e.g. on the tensor cores) */
     GL_ERR_STATE = -8           /* call out of order (e.g. solve before setup) */
 };
 
@@ -87,6 +87,17 @@ typedef struct {
  *   elem_mat per-element material index (into the same table as layer_mat)
  *            overriding the element's layer, length nx*ny*nz, or NULL: e.g.
  *            resin strips along the free edges of the width (Section 3).
+ *   element  0: 27-node triquadratic Q2 hexahedra; 1: the 20-node serendipity
+ *            hexahedra of Section 2.1 (the paper's element: vertices and edge
+ *            midpoints, full 3x3x3 Gauss integration).  The serendipity mesh
+ *            keeps the Q2 node numbering: its nodes are the grid nodes with at
+ *            most one odd index, and the other (face- and body-centre) entries
+ *            of every N-vector are not unknowns -- the solver eliminates them,
+ *            gl_solve and gl_solve_increment return there the values of the
+ *            serendipity field (so the vector is also its Q2 representation),
+ *            and the other calls ignore what they hold on input, except
+ *            gl_stress_noalloc, which reads u as given.  Not available in
+ *            gl_batch_*.
  * Material axes: R = R_l(psi + theta_e) R_r(phi), psi the frame angle at the
  * element centre (0 on limb 1 and flat plates), C_e constant per element. */
 typedef struct {
@@ -102,6 +113,7 @@ typedef struct {
     const double *theta_e;
     const double *node_dr;
     const int *elem_mat;
+    int element;               /* 0 Q2, 1 serendipity-20 */
 } gl_mesh;
 
 /* Solver options.
@@ -131,12 +143,18 @@ typedef struct {
  *              4e10.  The random start vectors of the subspace iteration are
  *              drawn per group, so another grouping changes the eigenvectors
  *              within the eigensolver's convergence, not the solution of a
- *              converged solve beyond its tolerance. */
+ *              converged solve beyond its tolerance.
+ *   fp32_update  GL_PREC_MIXED only: how the FP32 local factorisation updates
+ *              its trailing matrices.  0 (default): 128-column panels whose
+ *              rank-128 trailing updates run on the tensor cores (tcgen05,
+ *              TF32 inputs split hi + lo, FP32 accumulation: FP32-level
+ *              accuracy); 1: rank-32 updates on the FP32 CUDA cores. */
 typedef struct {
     int px, py, pz, overlap, nev, max_iter, precision, resid_period;
     double tol, sigma;
     int eig_iters;
     double factor_ws_bytes, eig_group_bytes;
+    int fp32_update;
 } gl_opts;
 
 /* Results of one solve.  rel_resid_true = ||f - K u||_2 / ||f||_2 on the
@@ -188,6 +206,16 @@ int gl_rhs(gl_ctx *ctx, double *f);
  * u (length N, out) holds the full displacement, prescribed values included.
  * info may be NULL. */
 int gl_solve(gl_ctx *ctx, const double *f, double *u, gl_info *info);
+
+/* Increment of a solution whose prescribed values are already in place: PCG
+ * solve of K_ff du_f = g_f with du = 0 on the Dirichlet DOFs (g of length N,
+ * required; its Dirichlet entries are ignored), stopping when
+ * ||g_f - K_ff du_f|| <= tol ||g_f||.  For a change of the stiffness K -> K',
+ * u' = u + du with g = f - K' u solves the new problem; with the residual of
+ * u left out, g = -(K' - K) u, du is the change of u to first order in the
+ * solver tolerance of du alone (used for finite differences with respect to
+ * theta_e, where only element e contributes to g). */
+int gl_solve_increment(gl_ctx *ctx, const double *g, double *du, gl_info *info);
 
 /* Stress recovery at element centres (Section 2.2 notation): s33 = sigma_rr,
  * t13 = tau_rs in the local (s, l, r) frame, length nx*ny*nz each (either may
@@ -332,6 +360,15 @@ typedef struct {
 int gl_profile(gl_ctx *ctx, int enable);
 int gl_profile_read(gl_ctx *ctx, gl_profile_data *out);
 long long gl_kernel_launches(void);
+
+/* FP64 FMA throughput of device `device`, measured: every thread of 8 blocks
+ * of 256 per SM runs 8 independent chains of `iters` dependent FP64 FMAs
+ * (no memory traffic), `reps` timed launches after one warm-up, CUDA events
+ * on a stream of its own.  flops_per_s = 2 x FMAs / time; n_sm (may be NULL)
+ * = the device's multiprocessor count; ms (may be NULL) = the timed span.
+ * This is the peak against which the FP64-bound kernels (K u, FP64 local
+ * sweeps) report their fraction. */
+int gl_fp64_peak_probe(int device, int iters, int reps, double *flops_per_s, int *n_sm, double *ms);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@
 
 #include "factor.h"
 #include "q2.cuh"
+#include "serendipity.h"
 
 namespace gl {
 
@@ -30,26 +31,6 @@ constexpr int NB = 32;        // pivot block
 constexpr int TILE = 64;      // trailing-update tile
 
 // ----------------------------------------------------------------- plan
-
-// A kernel's dynamic shared-memory limit is an attribute of the device that
-// is current when it is set, so the limit already raised is kept per device.
-struct SmemLimit {
-    static constexpr int MAX_DEVICES = 64;
-    std::mutex mu;
-    size_t set[MAX_DEVICES] = {};
-};
-
-template <class F>
-static void raise_smem_limit(SmemLimit &L, size_t need, F apply) {
-    int dev = 0;
-    GL_CUDA(cudaGetDevice(&dev));
-    GL_REQUIRE(dev >= 0 && dev < SmemLimit::MAX_DEVICES, "device index out of range");
-    std::lock_guard<std::mutex> lock(L.mu);
-    if (need > L.set[dev]) {
-        apply(need);
-        L.set[dev] = need;
-    }
-}
 
 void sweep_smem_for_plan(int max_f);
 
@@ -151,7 +132,8 @@ __global__ void __launch_bounds__(256) k_assemble(const int *__restrict__ fronts
                                                   const int *__restrict__ pair_elem,
                                                   const int16_t *__restrict__ pair_pos, const int *__restrict__ rows,
                                                   const double *__restrict__ C, const double *__restrict__ geo,
-                                                  const double *__restrict__ xi, double sigma, T *__restrict__ ws) {
+                                                  const double *__restrict__ xi, double sigma, int s20,
+                                                  T *__restrict__ ws) {
     const FrontDesc d = D[fronts[blockIdx.x]];
     const int pr_i = blockIdx.y;
     if (pr_i >= d.n_pairs) return;
@@ -214,6 +196,35 @@ __global__ void __launch_bounds__(256) k_assemble(const int *__restrict__ fronts
         for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x, ++slot) sK[idx] = acc[slot];
     }
     __syncthreads();
+    if (s20) {
+        // serendipity element: K <- P^T K P, P the identity on the 20 nodes and the fixed
+        // combinations of them on the 7 face/body centres; first the columns, then the rows
+        // (only master rows and columns are updated; the slaves' are never assembled)
+        for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x) {
+            const int r = idx / 81, col = idx % 81, a = col / 3, cc = col % 3;
+            if (s20_is_slave(a)) continue;
+            double v = sK[idx];
+            for (int b = 0; b < 27; ++b)
+                if (s20_is_slave(b)) {
+                    const double w = s20_weight(b, a);
+                    if (w != 0.0) v += w * sK[81 * r + 3 * b + cc];
+                }
+            sK[idx] = v;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x) {
+            const int r = idx / 81, col = idx % 81, a = r / 3, cc = r % 3;
+            if (s20_is_slave(a) || s20_is_slave(col / 3)) continue;
+            double v = sK[idx];
+            for (int b = 0; b < 27; ++b)
+                if (s20_is_slave(b)) {
+                    const double w = s20_weight(b, a);
+                    if (w != 0.0) v += w * sK[81 * (3 * b + cc) + col];
+                }
+            sK[idx] = v;
+        }
+        __syncthreads();
+    }
     T *F = ws + d.front_off;
     for (int idx = threadIdx.x; idx < 6561; idx += blockDim.x) {
         int c = idx / 81, r = idx % 81;    // column (pivot) c, row r
@@ -325,22 +336,37 @@ __global__ void k_trsm(const int *__restrict__ fronts, const FrontDesc *__restri
 
 // Trailing update of the lower triangle: F[r, c] -= sum_j P[r, j] P[c, j] for
 // r >= c >= k0+kb, P the panel columns k0..k0+kb.  64x64 tiles, 256 threads.
+// With cend > 0 only the columns c < min(cend, p) are updated (the rest of an
+// outer panel whose trailing matrix is updated separately): the tiles are
+// then those of the first column tiles of the trailing lower triangle.
 template <class T>
 __global__ void __launch_bounds__(256) k_syrk(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
-                                              T *__restrict__ ws, int k0) {
+                                              T *__restrict__ ws, int k0, int cend) {
     const FrontDesc d = D[fronts[blockIdx.x]];
     if (k0 >= d.p) return;
     const int kb = min(NB, d.p - k0), f = d.p + d.q;
     const int base = k0 + kb, m = f - base;
     if (m <= 0) return;
     const int nt = (m + TILE - 1) / TILE;
-    const int t = blockIdx.y;
-    if (t >= nt * (nt + 1) / 2) return;
-    // t -> (ti, tj), ti >= tj, row-major over the lower triangle of tiles
-    int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-    while (ti * (ti + 1) / 2 > t) --ti;
-    const int tj = t - ti * (ti + 1) / 2;
+    int t = blockIdx.y, ti, tj;
+    if (cend > 0) {
+        const int cw = min(cend, d.p) - base;       // columns to update
+        if (cw <= 0) return;
+        const int ncw = (cw + TILE - 1) / TILE;
+        // t -> (ti, tj), column-major over the tiles of the first ncw tile columns
+        tj = 0;
+        while (tj < ncw && t >= nt - tj) t -= nt - tj++;
+        if (tj >= ncw) return;
+        ti = tj + t;
+    } else {
+        if (t >= nt * (nt + 1) / 2) return;
+        // t -> (ti, tj), ti >= tj, row-major over the lower triangle of tiles
+        ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while (ti * (ti + 1) / 2 > t) --ti;
+        tj = t - ti * (ti + 1) / 2;
+    }
+    const int cmax = cend > 0 ? min(cend, d.p) : f;   // columns c < cmax are updated
     const int r0 = base + ti * TILE, c0 = base + tj * TILE;
     T *F = ws + d.front_off;
     __shared__ T sa[NB][TILE + 1], sb[NB][TILE + 1];
@@ -374,7 +400,7 @@ __global__ void __launch_bounds__(256) k_syrk(const int *__restrict__ fronts, co
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             int r = r0 + tx + 16 * a, c = c0 + ty + 16 * b;
-            if (r < f && c < f && r >= c) F[r + (int64_t)c * f] -= acc[a][b];
+            if (r < f && c < cmax && r >= c) F[r + (int64_t)c * f] -= acc[a][b];
         }
 }
 
@@ -392,9 +418,35 @@ __global__ void k_copy_panel(const int *__restrict__ fronts, const FrontDesc *__
     }
 }
 
+// Blocked right-looking partial Cholesky of the p pivot columns of every front
+// of a level.  FP64 (and FP32 with tc = false): blocks of NB = 32 pivots, each
+// followed by the rank-32 update of the whole trailing lower triangle.  FP32
+// with tc: outer panels of 128 columns factored with the same 32-wide steps,
+// whose updates stay inside the panel, and one rank-128 update of the trailing
+// matrix per panel on the tensor cores (syrk_tc.cu) -- four times the flops
+// per byte of trailing matrix read and written.
 static void partial_cholesky_level(const int *d_fronts, int n_fronts, const FrontDesc *d_fr, int max_p, int max_f,
                                    void *ws, bool fp32, int *d_err, cudaStream_t s, double drop = 0.0,
-                                   int *d_drops = nullptr) {
+                                   int *d_drops = nullptr, bool tc = false) {
+    if (fp32 && tc) {
+        const int PW = syrk_tc_panel();
+        for (int k0 = 0; k0 < max_p; k0 += PW) {
+            const int kend = k0 + PW;
+            for (int k1 = k0; k1 < std::min(kend, max_p); k1 += NB) {
+                const int rows = std::max(1, max_f - k1);
+                const int m = max_f - k1;
+                const int nt = m > 0 ? (m + TILE - 1) / TILE : 0;
+                const int ncw = std::min(nt, (kend - k1 - 1) / TILE + 1);    // column tiles inside the panel
+                const int tiles = std::max(1, ncw * nt - ncw * (ncw - 1) / 2);
+                k_potrf<float><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k1, d_err, (float)drop, d_drops);
+                k_trsm<float><<<dim3(n_fronts, (rows + 127) / 128), 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k1);
+                k_syrk<float><<<dim3(n_fronts, tiles), 256, 0, s>>>(d_fronts, d_fr, (float *)ws, k1, kend);
+                GL_CUDA(cudaGetLastError());
+            }
+            syrk_tc_level(d_fronts, n_fronts, d_fr, k0, max_f, (float *)ws, d_err, s);
+        }
+        return;
+    }
     for (int k0 = 0; k0 < max_p; k0 += NB) {
         // upper bounds over the level's fronts (a front's last pivot block may be short)
         int rows = std::max(1, max_f - k0);
@@ -405,11 +457,11 @@ static void partial_cholesky_level(const int *d_fronts, int n_fronts, const Fron
         if (fp32) {
             k_potrf<float><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k0, d_err, (float)drop, d_drops);
             k_trsm<float><<<gt, 128, 0, s>>>(d_fronts, d_fr, (float *)ws, k0);
-            k_syrk<float><<<gs, 256, 0, s>>>(d_fronts, d_fr, (float *)ws, k0);
+            k_syrk<float><<<gs, 256, 0, s>>>(d_fronts, d_fr, (float *)ws, k0, 0);
         } else {
             k_potrf<double><<<n_fronts, 128, 0, s>>>(d_fronts, d_fr, (double *)ws, k0, d_err, drop, d_drops);
             k_trsm<double><<<gt, 128, 0, s>>>(d_fronts, d_fr, (double *)ws, k0);
-            k_syrk<double><<<gs, 256, 0, s>>>(d_fronts, d_fr, (double *)ws, k0);
+            k_syrk<double><<<gs, 256, 0, s>>>(d_fronts, d_fr, (double *)ws, k0, 0);
         }
         GL_CUDA(cudaGetLastError());
     }
@@ -546,7 +598,8 @@ void numeric_factor(FactorPlan &P, const double *C, const double *geo, const dou
             GL_CUDA(cudaMemsetAsync(W, 0, lev_ws[dpt] * sizeof(T), s));
             if (max_pairs[dpt] > 0) {
                 k_assemble<T><<<dim3(nf, max_pairs[dpt]), 256, 6561 * 8, s>>>(
-                    d_lev[dpt].p, d_fr.p, P.d_pair_elem.p, P.d_pair_pos.p, P.d_rows.p, C, geo, xi, sigma, W);
+                    d_lev[dpt].p, d_fr.p, P.d_pair_elem.p, P.d_pair_pos.p, P.d_rows.p, C, geo, xi, sigma, P.s20 ? 1 : 0,
+                    W);
                 GL_CUDA(cudaGetLastError());
             }
             if (dpt + 1 < nlev) {
@@ -559,7 +612,8 @@ void numeric_factor(FactorPlan &P, const double *C, const double *geo, const dou
                     GL_CUDA(cudaGetLastError());
                 }
             }
-            partial_cholesky_level(d_lev[dpt].p, nf, d_fr.p, max_p[dpt], max_f[dpt], W, sizeof(T) == 4, d_err, s);
+            partial_cholesky_level(d_lev[dpt].p, nf, d_fr.p, max_p[dpt], max_f[dpt], W, sizeof(T) == 4, d_err, s,
+                                   0.0, nullptr, sizeof(T) == 4 && P.tc_update);
             int gy = (int)std::min<int64_t>(std::max<int64_t>(1, (max_panel[dpt] + 255) / 256), 4096);
             k_copy_panel<T><<<dim3(nf, gy), 256, 0, s>>>(d_lev[dpt].p, d_fr.p, W, L);
             GL_CUDA(cudaGetLastError());
@@ -708,10 +762,16 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_fwd(const int *__restrict
 // Backward substitution for the fronts of one level, one CTA per front: for
 // each block B of 32 pivots from the last to the first,
 //   x_B = L[B,B]^{-T} y_B - W[i,B]^T x_i   (rows i below B),
-// one reduction down each column of the block over the rows from B to the end
-// of the front (the rows of B with +, the rows below with -); warp w owns the
-// columns w, w + 8, ..., its lanes stride the rows with 8 loads in flight, and
-// a shuffle tree adds the lanes.  No serial triangular solve remains.
+// i.e. one sum down each column of the block over the rows from B to the end
+// of the front (the rows of B with +, the rows below with -).  The rows of B
+// are negated in shared memory first, so every row enters the sum with the
+// same sign and x_B = -(sum).  Warp w takes the row tiles w, w + nw, ... of
+// 32 rows: lane l loads row r0 + l of the 32 columns (coalesced per column)
+// into registers, writes it transposed into the warp's 32 x 33 tile, and then
+// lane j accumulates column j over the tile's 32 rows from shared memory --
+// one FMA per nonzero and no per-column shuffle reduction; the next tile's
+// loads are in flight meanwhile.  The nw partial sums of each column are added
+// once per block.  No serial triangular solve remains.
 template <class T, int NR>
 __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
                                              const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
@@ -719,8 +779,10 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict
     extern __shared__ unsigned char smraw[];
     const FrontDesc d = D[fronts[blockIdx.x]];
     const int p = d.p, f = d.p + d.q, n = d.vlen;
-    T *v = reinterpret_cast<T *>(smraw);
-    T *red = v + (int64_t)f * NR;   // 32 x NR column results of the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *v = reinterpret_cast<T *>(smraw);      // the front's vector, f x NR
+    T *red = v + (int64_t)f * NR;               // NR x nw x 32 partial column sums
+    T *tile = red + 32 * NR * nw + warp * (32 * 33);   // this warp's transposed row tile
     T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
     for (int i = threadIdx.x; i < f; i += blockDim.x)
 #pragma unroll
@@ -729,47 +791,66 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict
     __syncthreads();
     if (p == 0) return;
     const T *Lp = L + d.l_off;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int jb = ((p - 1) / 32) * 32; jb >= 0; jb -= 32) {
+    int jb = ((p - 1) / 32) * 32;
+    if (threadIdx.x < 32 * NR) {
+        const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
+        if (j < min(32, p - jb)) v[jb + j + r * f] = -v[jb + j + r * f];
+    }
+    __syncthreads();
+    for (; jb >= 0; jb -= 32) {
         const int kb = min(32, p - jb);
-        for (int j = warp; j < kb; j += nw) {
-            const T *col = Lp + (int64_t)(jb + j) * f;
-            T acc[NR];
-            {
-                // rows of B: L[B,B]^{-1}[i, j] y_i for i >= j, negated here and restored below
-                const bool in = lane >= j && lane < kb;
-                const T l = in ? col[jb + lane] : T(0);
+        const T *cb = Lp + (int64_t)jb * f;      // column jb + j starts at cb + j f
+        T acc[NR], acc2[NR];   // two chains of FMAs per column
 #pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] = -(l * v[jb + (in ? lane : 0) + r * f]);
-            }
-            int i = jb + kb + lane;
-            // rows below B: + W[i, j] x_i, 8 independent loads per lane in flight
-            for (; i + 7 * 32 < f; i += 8 * 32) {
-                T l[8];
+        for (int r = 0; r < NR; ++r) acc[r] = acc2[r] = T(0);
+        T w[32];
+        int r0 = jb + 32 * warp;
+        if (r0 < f) {
+            const int i = r0 + lane;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) l[t] = col[i + 32 * t];
-#pragma unroll
-                for (int t = 0; t < 8; ++t)
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[r] += l[t] * v[i + 32 * t + r * f];
-            }
-            for (; i < f; i += 32) {
-                const T l = col[i];
-#pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] += l * v[i + r * f];
-            }
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                T a = acc[r];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (lane == 0) red[j + 32 * r] = -a;
-            }
+            for (int j = 0; j < 32; ++j) w[j] = (i < f && j < kb) ? cb[i + (int64_t)j * f] : T(0);
         }
+        for (; r0 < f; r0 += 32 * nw) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tile[j * 33 + lane] = w[j];
+            __syncwarp();
+            const int rn = r0 + 32 * nw;
+            if (rn < f) {
+                const int i = rn + lane;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) w[j] = (i < f && j < kb) ? cb[i + (int64_t)j * f] : T(0);
+            }
+            const int cnt = min(32, f - r0);
+            const T *tl = tile + lane * 33;
+            if (cnt == 32) {
+#pragma unroll
+                for (int ii = 0; ii < 32; ii += 2) {
+                    const T t0 = tl[ii], t1 = tl[ii + 1];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        acc[r] += t0 * v[r0 + ii + r * f];
+                        acc2[r] += t1 * v[r0 + ii + 1 + r * f];
+                    }
+                }
+            } else {
+                for (int ii = 0; ii < cnt; ++ii) {
+                    const T t = tl[ii];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[r] += t * v[r0 + ii + r * f];
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) red[(r * nw + warp) * 32 + lane] = acc[r] + acc2[r];
         __syncthreads();
         if (threadIdx.x < 32 * NR) {
             const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
-            if (j < kb) v[jb + j + r * f] = red[j + 32 * r];
+            T s = T(0);
+            for (int ww = 0; ww < nw; ++ww) s += red[(r * nw + ww) * 32 + j];
+            if (j < kb) v[jb + j + r * f] = -s;
+            // the next block's rows (read from the next step on) enter its sum negated
+            if (jb >= 32) v[jb - 32 + j + r * f] = -v[jb - 32 + j + r * f];
         }
         __syncthreads();
     }
@@ -778,9 +859,12 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict
         for (int r = 0; r < NR; ++r) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
 }
 
-// Shared memory of the sweeps: static tiles plus the dynamic front vector and
-// staging area.  The dynamic limit is raised per kernel and device to the largest front
-// seen; build_plan calls sweep_smem_for_plan for every variant, so no
+// Shared memory of the sweeps.  Forward: the front vector (f x NR) and the
+// copy of x_B (32 x NR), plus the static inverse block.  Backward: the front
+// vector, the partial column sums (NR x nw x 32) and one 32 x 33 tile per warp,
+// so its block size shrinks on levels whose largest front would not fit.  The
+// dynamic limit of every variant is raised once per device to all that a CTA
+// may hold; build_plan calls sweep_smem_for_plan for every variant, so no
 // attribute is ever changed while a stream is being captured.
 constexpr size_t SMEM_PER_CTA = 227 * 1024;
 
@@ -796,20 +880,42 @@ static size_t sweep_static_smem() {
 }
 
 template <class T, int NR>
-static size_t sweep_dyn_smem(int max_f) {
-    return ((size_t)std::max(max_f, 1) + 32) * NR * sizeof(T);
+static size_t fwd_dyn_smem(int f) {
+    return ((size_t)std::max(f, 1) + 32) * NR * sizeof(T);
+}
+
+template <class T, int NR>
+static size_t bwd_dyn_smem(int f, int nthreads) {
+    const size_t nw = (size_t)nthreads / 32;
+    return ((size_t)std::max(f, 1) * NR + 32 * NR * nw + 33 * 32 * nw) * sizeof(T);
+}
+
+template <class T, int NR>
+constexpr int bwd_min_threads() {
+    return 32 * NR;   // the column sums of the block are finished by 32 NR threads
 }
 
 template <class T, int NR>
 static bool sweep_fits(int max_f) {
-    return sweep_dyn_smem<T, NR>(max_f) + sweep_static_smem<T, NR>() <= SMEM_PER_CTA;
+    const size_t lim = SMEM_PER_CTA - sweep_static_smem<T, NR>();
+    return fwd_dyn_smem<T, NR>(max_f) <= lim && bwd_dyn_smem<T, NR>(max_f, bwd_min_threads<T, NR>()) <= lim;
+}
+
+// Threads per CTA of the backward sweep on a level: the wanted count, halved
+// while the level's largest front does not fit.
+template <class T, int NR>
+static int bwd_threads(int max_f, int want) {
+    const size_t lim = SMEM_PER_CTA - sweep_static_smem<T, NR>();
+    int nt = want;
+    while (nt > bwd_min_threads<T, NR>() && bwd_dyn_smem<T, NR>(max_f, nt) > lim) nt /= 2;
+    return nt;
 }
 
 template <class T, int NR>
 static void ensure_sweep_smem(int max_f) {
     static SmemLimit limit;
     if (!sweep_fits<T, NR>(max_f)) return;
-    raise_smem_limit(limit, sweep_dyn_smem<T, NR>(max_f), [](size_t v) {
+    raise_smem_limit(limit, SMEM_PER_CTA - sweep_static_smem<T, NR>(), [](size_t v) {
         GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
         GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
     });
@@ -831,15 +937,15 @@ static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c
     for (int dpt = nlev - 1; dpt >= 0; --dpt) {
         const Level &Lv = P.levels[dpt];
         if (Lv.fronts.empty()) continue;
-        const size_t sm = sweep_dyn_smem<T, NR>(Lv.max_f);
+        const size_t sm = fwd_dyn_smem<T, NR>(Lv.max_f);
         const int nt = Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256;
         k_fwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
     }
     for (int dpt = 0; dpt < nlev; ++dpt) {
         const Level &Lv = P.levels[dpt];
         if (Lv.fronts.empty()) continue;
-        const size_t sm = sweep_dyn_smem<T, NR>(Lv.max_f);
-        const int nt = Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256;
+        const int nt = bwd_threads<T, NR>(Lv.max_f, Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256);
+        const size_t sm = bwd_dyn_smem<T, NR>(Lv.max_f, nt);
         k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
     }
     GL_CUDA(cudaGetLastError());

@@ -3,9 +3,35 @@
 // solves of the overlapping Schwarz preconditioner).
 #pragma once
 
+#include <mutex>
+
 #include "gl_internal.h"
 
 namespace gl {
+
+// A kernel's dynamic shared-memory limit is an attribute of the device that
+// is current when it is set, so the limit already raised is kept per device.
+struct SmemLimit {
+    static constexpr int MAX_DEVICES = 64;
+    std::mutex mu;
+    size_t set[MAX_DEVICES] = {};
+    template <class F>
+    void ensure(size_t need, F apply) {
+        int dev = 0;
+        GL_CUDA(cudaGetDevice(&dev));
+        GL_REQUIRE(dev >= 0 && dev < MAX_DEVICES, "device index out of range");
+        std::lock_guard<std::mutex> lock(mu);
+        if (need > set[dev]) {
+            apply(need);
+            set[dev] = need;
+        }
+    }
+};
+
+template <class F>
+inline void raise_smem_limit(SmemLimit &L, size_t need, F apply) {
+    L.ensure(need, apply);
+}
 
 // Per supernode, flattened over all subdomains of one plan.
 struct FrontDesc {
@@ -38,6 +64,8 @@ struct FactorPlan {
     int64_t ws_max = 0;
     int max_f = 0;
     double ws_budget_bytes = 6e9;            // numeric_factor: workspace per buffer (subdomain groups fit it)
+    bool tc_update = true;                   // FP32 factors: trailing updates on the tensor cores
+    bool s20 = false;                        // serendipity elements: element matrices P^T K_Q2 P
     int last_groups = 0;                     // groups the last numeric_factor used
     // device
     DBuf<FrontDesc> d_fr;
@@ -59,6 +87,14 @@ void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_
 template <class T>
 void numeric_factor(FactorPlan &P, const double *C, const double *geo, const double *xi, double sigma, T *L, int *d_err,
                     cudaStream_t s);
+
+// Trailing update of an FP32 level on the tensor cores (syrk_tc.cu): for every
+// front with kw = min(syrk_tc_panel(), p - k0) factored panel columns
+// [k0, k0 + kw), F[r, c] -= sum_k F[r, k] F[c, k] over base = k0 + kw <= c <= r.
+// d_err is set to 2 if a tensor-core wait gave up.
+int syrk_tc_panel();
+void syrk_tc_level(const int *d_fronts, int n_fronts, const FrontDesc *d_fr, int k0, int max_f, float *ws,
+                   int *d_err, cudaStream_t s);
 
 // x <- L^{-T} L^{-1} x (L as factored; stored in partitioned-inverse form)
 // for local multi-vectors of kcols columns per subdomain,

@@ -20,12 +20,18 @@ struct Error {
 
 [[noreturn]] void fail(int code, const std::string &msg);
 
+// A failed runtime call also leaves its error recorded as the thread's last
+// error; it is read back (cleared) before failing, so that a recoverable error
+// such as an allocation failure does not resurface at the next
+// cudaGetLastError() of a later call.
 #define GL_CUDA(x)                                                                   \
     do {                                                                             \
         cudaError_t e_ = (x);                                                        \
-        if (e_ != cudaSuccess)                                                       \
+        if (e_ != cudaSuccess) {                                                     \
+            cudaGetLastError();                                                      \
             ::gl::fail(e_ == cudaErrorMemoryAllocation ? GL_ERR_OOM : GL_ERR_CUDA,   \
                        std::string(#x) + ": " + cudaGetErrorString(e_));             \
+        }                                                                            \
     } while (0)
 
 #define GL_REQUIRE(cond, msg)                                                        \
@@ -92,6 +98,7 @@ struct MeshHost {
     int nx = 0, ny = 0, nz = 0, NX = 0, NY = 0, NZ = 0;
     int64_t n_nodes = 0, n_dof = 0, n_elem = 0;
     int geometry = 0;
+    int element = 0;                         // 0 Q2 (27 nodes), 1 serendipity (20 nodes; serendipity.h)
     double R_inner = 0, limb_L = 0, arc_rad = 0;
     std::vector<double> sv, lv, rv;          // vertex coordinates (rv = depth from inner face)
     std::vector<double> tn, ln, rn;          // Q2 node parameters
@@ -155,6 +162,8 @@ void launch_stress(const MeshHost &m, const double *X, const double *C, const do
                    const double *u, double *s33, double *t13, cudaStream_t s);
 void launch_failure(const MeshHost &m, const double *X, const double *C, const double *psi_x, const uint8_t *resin,
                     const double *u, double s33a, double s13a, double *F, unsigned long long *best, cudaStream_t s);
+// FP64 FMA probe on the current device (probe.cu): flops per second.
+double fp64_probe(int iters, int reps, int *n_sm, double *ms_out);
 // Fails with GL_ERR_INVALID_ARG unless [p, p + bytes) lies inside one device
 // allocation (cuMemGetAddressRange; no allocation is made).
 void require_device_span(const void *p, size_t bytes, const char *what);

@@ -174,6 +174,7 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
     std::vector<SubSymbolic> syms;
     problem_symbolic(P, true, leaf_nodes, syms);
     build_plan(syms, out.PN, s);
+    out.PN.s20 = PD.s20;
     P.stamp("Neumann symbolic");
     FactorPlan &PN = out.PN;
     for (int j = 0; j < nsub; ++j)
@@ -224,6 +225,7 @@ void problem_coarse(const Problem &P, const gl_opts &o, const FactorPlan &PD, in
         FactorPlan PG;
         build_plan(gs, PG, s);
         PG.ws_budget_bytes = PD.ws_budget_bytes;
+        PG.s20 = PD.s20;
         gs.clear();
         const int64_t goff = PN.vec_off[j0], gl = PG.n_local;
         DBuf<double> LN;

@@ -17,6 +17,7 @@
 #include <thread>
 
 #include "problem.h"
+#include "serendipity.h"
 
 namespace gl {
 
@@ -128,6 +129,8 @@ struct gl_ctx {
     DBuf<double> cvec2;
     // work
     DBuf<double> x, r, z, p, q, ud, fe, partials, cvec, xl64;
+    DBuf<double> ks;     // serendipity: the filled copy of K u's input
+    int64_t n_dir = 0;   // entries of d_dir_dof / d_dir_val: the prescribed DOFs (and the serendipity slaves)
     DBuf<float> xl32;
     DBuf<CGScalars> S;
     DBuf<int> err;
@@ -179,6 +182,7 @@ void check_err(gl_ctx *c, const char *what) {
     GL_CUDA(cudaStreamSynchronize(c->stream));
     if (h) {
         c->err.zero(c->stream);
+        if (h == 2) fail(GL_ERR_TIMEOUT, std::string(what) + ": a tensor-core wait gave up");
         fail(GL_ERR_NOT_SPD, std::string(what) + ": non-positive pivot");
     }
 }
@@ -209,6 +213,9 @@ void build_geometry(gl_ctx *c) {
     if (!m.node_dr.empty()) c->d_dr.upload(m.node_dr, s);
     else c->d_dr.release();
     launch_node_coords(m, c->d_tn.p, c->d_ln.p, c->d_rn.p, m.node_dr.empty() ? nullptr : c->d_dr.p, c->d_X.p, s);
+    // serendipity: face and body centres at the serendipity interpolation of the element's nodes, so that
+    // the Q2 geometry map of the element is its serendipity map
+    if (m.element == 1) s20_fill(m, c->d_X.p, s);
     c->psi_x.assign(m.nx, 0.0);
     if (m.geometry == 1)
         for (int ex = 0; ex < m.nx; ++ex) {
@@ -238,6 +245,7 @@ void build_geometry(gl_ctx *c) {
     c->d_ftrac.alloc(m.n_dof);
     c->d_ftrac.zero(s);
     for (auto &t : c->tractions) launch_traction(m, c->d_X.p, t.first, t.second.data(), c->d_ftrac.p, s);
+    if (m.element == 1) s20_fold(m, c->d_ftrac.p, s);            // f_20 = P^T f_Q2
     GL_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -274,7 +282,16 @@ int64_t factor_solve_launches(const FactorPlan &P) {
 
 void apply_K(gl_ctx *c, const double *x, double *y) {
     prof_begin(c, PH_KU);
-    launch_ku(c->m, c->d_C.p, c->d_geo.p, x, y, c->stream);
+    if (c->m.element == 1) {
+        // serendipity: y = P^T K_Q2 P x (slave entries of x filled in a copy, folded out of y)
+        GL_CUDA(cudaMemcpyAsync(c->ks.p, x, c->m.n_dof * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        s20_fill(c->m, c->ks.p, c->stream);
+        launch_ku(c->m, c->d_C.p, c->d_geo.p, c->ks.p, y, c->stream);
+        s20_fold(c->m, y, c->stream);
+        g_launches += 2;
+    } else {
+        launch_ku(c->m, c->d_C.p, c->d_geo.p, x, y, c->stream);
+    }
     prof_end(c, PH_KU);
     g_launches += 1;
 }
@@ -324,6 +341,7 @@ void setup(gl_ctx *c, const gl_opts &o) {
     GL_REQUIRE(o.nev >= 0 && o.nev <= 28, "nev must be in [0, 28]");
     GL_REQUIRE(o.px <= c->m.nx && o.py <= c->m.ny && o.pz <= c->m.nz, "more subdomains than elements along an axis");
     GL_REQUIRE(o.precision == GL_PREC_FP64 || o.precision == GL_PREC_MIXED, "unknown precision mode");
+    GL_REQUIRE(o.fp32_update == 0 || o.fp32_update == 1, "fp32_update must be 0 or 1");
     c->ready = false;
     c->opts = o;
     if (c->opts.max_iter <= 0) c->opts.max_iter = 2000;
@@ -340,6 +358,36 @@ void setup(gl_ctx *c, const gl_opts &o) {
     stamp(c, "geometry, materials, loads");
     std::vector<uint8_t> is_dir(m.n_dof, 0);
     for (int64_t d : c->dir_dof) is_dir[d] = 1;
+    {
+        // the solver's eliminated DOFs: the prescribed ones with their values, and for the
+        // serendipity element the slave entries with 0 (a prescribed value there is ignored:
+        // the serendipity field fixes it)
+        std::vector<int64_t> dd(c->dir_dof);
+        std::vector<double> dv(c->dir_val);
+        if (m.element == 1) {
+            std::vector<int64_t> sl = s20_slave_dofs(m);
+            std::vector<uint8_t> is_slave(m.n_dof, 0);
+            for (int64_t d : sl) is_slave[d] = 1;
+            dd.clear();
+            dv.clear();
+            size_t k = 0;
+            for (int64_t d = 0; d < m.n_dof; ++d) {
+                while (k < c->dir_dof.size() && c->dir_dof[k] < d) ++k;
+                const bool pres = k < c->dir_dof.size() && c->dir_dof[k] == d;
+                if (is_slave[d]) {
+                    dd.push_back(d);
+                    dv.push_back(0.0);
+                    is_dir[d] = 1;
+                } else if (pres) {
+                    dd.push_back(d);
+                    dv.push_back(c->dir_val[k]);
+                }
+            }
+        }
+        c->d_dir_dof.upload(dd, s);
+        c->d_dir_val.upload(dv, s);
+        c->n_dir = (int64_t)dd.size();
+    }
     c->n_free = m.n_dof - (int64_t)std::count(is_dir.begin(), is_dir.end(), (uint8_t)1);
     // the laminate as a one-part problem
     Problem &P = c->prob;
@@ -367,6 +415,8 @@ void setup(gl_ctx *c, const gl_opts &o) {
         build_plan(syms, c->PD, s);
     }
     c->PD.ws_budget_bytes = c->opts.factor_ws_bytes > 0 ? c->opts.factor_ws_bytes : 6e9;
+    c->PD.tc_update = c->opts.fp32_update == 0;
+    c->PD.s20 = m.element == 1;
     stamp(c, "Dirichlet symbolic");
     if (std::getenv("GL_VERBOSE")) {
         // per dissection level: fronts, factor nonzeros the sweeps touch, the largest front
@@ -403,6 +453,8 @@ void setup(gl_ctx *c, const gl_opts &o) {
         std::fprintf(stderr, "[gl]   %d dependent coarse columns dropped\n", c->co.n_dropped);
     // work vectors
     const int64_t N = m.n_dof;
+    if (m.element == 1) c->ks.alloc(N);
+    else c->ks.release();
     for (DBuf<double> *b : {&c->x, &c->r, &c->z, &c->p, &c->q, &c->ud, &c->fe}) b->alloc(N);
     c->partials.alloc(1024);
     c->cvec.alloc(std::max(1, c->co.n0));
@@ -430,7 +482,7 @@ double read_scalar(gl_ctx *c, const double *d) {
 // Effective right-hand side fe = f - K u_D on the free DOFs, 0 on Dirichlet DOFs.
 void prepare_rhs(gl_ctx *c, const double *f, bool homogeneous) {
     cudaStream_t s = c->stream;
-    const int64_t N = c->m.n_dof, nd = (int64_t)c->dir_dof.size();
+    const int64_t N = c->m.n_dof, nd = c->n_dir;
     if (f) to_device(c->fe.p, f, N, s);
     else GL_CUDA(cudaMemcpyAsync(c->fe.p, c->d_ftrac.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     c->ud.zero(s);
@@ -445,7 +497,7 @@ void prepare_rhs(gl_ctx *c, const double *f, bool homogeneous) {
 void solve(gl_ctx *c, const double *f, double *u, gl_info *info, bool homogeneous = false) {
     if (!c->ready) fail(GL_ERR_STATE, "gl_solve before gl_setup");
     cudaStream_t s = c->stream;
-    const int64_t N = c->m.n_dof, nd = (int64_t)c->dir_dof.size();
+    const int64_t N = c->m.n_dof, nd = c->n_dir;
     cudaEvent_t e0, e1;
     GL_CUDA(cudaEventCreate(&e0));
     GL_CUDA(cudaEventCreate(&e1));
@@ -537,6 +589,10 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info, bool homogeneou
     const double rt = read_scalar(c, &S->rr);
     axpy(c->x.p, 1.0, c->ud.p, N, s);
     g_launches += nds + 4;
+    if (c->m.element == 1) {
+        s20_fill(c->m, c->x.p, s);   // the serendipity field's values on the face and body centres
+        g_launches += 1;
+    }
     for (int ph = 0; ph < PH_N; ++ph) prof_fold(c, ph);
     GL_CUDA(cudaEventRecord(e1, s));
     from_device(u, c->x.p, N, s);
@@ -709,6 +765,7 @@ void batch_setup(gl_batch *b, const gl_opts &o) {
     GL_REQUIRE(o.overlap >= 1, "overlap must be >= 1");
     GL_REQUIRE(o.nev >= 0 && o.nev <= 28, "nev must be in [0, 28]");
     GL_REQUIRE(o.precision == GL_PREC_FP64 || o.precision == GL_PREC_MIXED, "unknown precision mode");
+    GL_REQUIRE(o.fp32_update == 0 || o.fp32_update == 1, "fp32_update must be 0 or 1");
     b->ready = false;
     b->opts = o;
     if (b->opts.max_iter <= 0) b->opts.max_iter = 2000;
@@ -812,6 +869,7 @@ void batch_setup(gl_batch *b, const gl_opts &o) {
         problem_symbolic(P, false, LEAF_NODES, syms);
         build_plan(syms, b->PD, s);
         b->PD.ws_budget_bytes = b->opts.factor_ws_bytes > 0 ? b->opts.factor_ws_bytes : 6e9;
+        b->PD.tc_update = b->opts.fp32_update == 0;
     }
     if (b->opts.precision == GL_PREC_MIXED) {
         b->LD64.release();
@@ -828,6 +886,7 @@ void batch_setup(gl_batch *b, const gl_opts &o) {
         GL_CUDA(cudaStreamSynchronize(s));
         if (h) {
             b->err.zero(s);
+            if (h == 2) fail(GL_ERR_TIMEOUT, "batch local Dirichlet factorisation: a tensor-core wait gave up");
             fail(GL_ERR_NOT_SPD, "batch local Dirichlet factorisation: non-positive pivot");
         }
     }
@@ -1081,6 +1140,7 @@ int gl_set_mesh(gl_ctx *c, const gl_mesh *mesh) {
         GL_REQUIRE(c->have_mat, "gl_set_materials must come before gl_set_mesh");
         GL_REQUIRE(mesh->nx >= 1 && mesh->ny >= 1 && mesh->nlayers >= 1, "empty mesh");
         GL_REQUIRE(mesh->geometry == 0 || mesh->geometry == 1, "geometry must be 0 or 1");
+        GL_REQUIRE(mesh->element == 0 || mesh->element == 1, "element must be 0 (Q2) or 1 (serendipity)");
         MeshHost m;
         m.nx = mesh->nx;
         m.ny = mesh->ny;
@@ -1113,6 +1173,7 @@ int gl_set_mesh(gl_ctx *c, const gl_mesh *mesh) {
         m.n_elem = (int64_t)m.nx * m.ny * m.nz;
         GL_REQUIRE(m.n_dof < (int64_t)1 << 31, "mesh too large for 32-bit local indices");
         m.geometry = mesh->geometry;
+        m.element = mesh->element;
         m.R_inner = mesh->R_inner;
         m.limb_L = mesh->limb_L;
         m.arc_rad = mesh->arc_deg * M_PI / 180.0;
@@ -1232,6 +1293,14 @@ int gl_solve(gl_ctx *c, const double *f, double *u, gl_info *info) {
     });
 }
 
+int gl_solve_increment(gl_ctx *c, const double *g, double *du, gl_info *info) {
+    return guard([&] {
+        require_ctx(c);
+        GL_REQUIRE(g && du, "null argument");
+        solve(c, g, du, info, true);                 // K_ff du_f = g_f, du = 0 on Dirichlet DOFs
+    });
+}
+
 int gl_stress(gl_ctx *c, const double *u, double *s33, double *t13, double *peak) {
     return guard([&] {
         require_ctx(c);
@@ -1242,6 +1311,7 @@ int gl_stress(gl_ctx *c, const double *u, double *s33, double *t13, double *peak
         DBuf<double> du, d33, d13, dpk;
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
+        if (m.element == 1) s20_fill(m, du.p, s);
         d33.alloc(m.n_elem);
         d13.alloc(m.n_elem);
         launch_stress(m, c->d_X.p, c->d_C.p, c->d_psi.p, du.p, d33.p, d13.p, s);
@@ -1306,7 +1376,7 @@ int gl_apply_prec(gl_ctx *c, const double *r, double *z) {
         GL_REQUIRE(r && z, "null vector");
         cudaStream_t s = c->stream;
         to_device(c->r.p, r, c->m.n_dof, s);
-        set_entries(c->r.p, c->d_dir_dof.p, (int64_t)c->dir_dof.size(), nullptr, s);
+        set_entries(c->r.p, c->d_dir_dof.p, c->n_dir, nullptr, s);
         apply_prec(c, c->r.p, c->z.p);
         from_device(z, c->z.p, c->m.n_dof, s);
     });
@@ -1326,6 +1396,7 @@ int gl_failure_index(gl_ctx *c, const double *u, double s33_allow, double s13_al
         DBuf<unsigned long long> best;
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
+        if (m.element == 1) s20_fill(m, du.p, s);
         dF.alloc(m.n_elem);
         best.alloc(1);
         launch_failure(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_resin.p, du.p, s33_allow, s13_allow, dF.p, best.p, s);
@@ -1367,6 +1438,7 @@ int gl_stress_vjp(gl_ctx *c, const double *u, const double *w33, const double *w
         DBuf<double> du, d33, d13, dgu, dgt;
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
+        if (m.element == 1) s20_fill(m, du.p, s);
         if (w33) {
             d33.alloc(m.n_elem);
             to_device(d33.p, w33, m.n_elem, s);
@@ -1383,6 +1455,7 @@ int gl_stress_vjp(gl_ctx *c, const double *u, const double *w33, const double *w
         launch_stress_vjp(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
                           c->d_layer_angle.p, c->d_theta.p, c->d_matC.p, du.p, d33.p, d13.p, dgu.p, dgt.p, s);
         g_launches += 1;
+        if (dJdu && m.element == 1) s20_fold(m, dgu.p, s);   // dJ/du_20 = P^T dJ/du_Q2
         if (dJdu) from_device(dJdu, dgu.p, m.n_dof, s);
         if (dJdth) from_device(dJdth, dgt.p, m.n_elem, s);
         GL_CUDA(cudaStreamSynchronize(s));
@@ -1401,6 +1474,7 @@ int gl_adjoint(gl_ctx *c, const double *u, const double *dJdu, double *grad, gl_
         solve(c, dJdu, lam.p, info, true);          // K_ff lambda = (dJ/du)_f, lambda = 0 on Dirichlet DOFs
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
+        if (m.element == 1) s20_fill(m, du.p, s);   // lambda comes back filled from solve()
         dg.alloc(m.n_elem);
         launch_adjoint_contract(m, c->d_geo.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
                                 c->d_layer_angle.p,
@@ -1461,6 +1535,18 @@ int gl_profile_read(gl_ctx *c, gl_profile_data *out) {
 
 long long gl_kernel_launches(void) { return g_launches.load(); }
 
+int gl_fp64_peak_probe(int device, int iters, int reps, double *flops_per_s, int *n_sm, double *ms) {
+    return guard([&] {
+        GL_REQUIRE(flops_per_s, "null output");
+        GL_REQUIRE(iters > 0 && reps > 0, "iters and reps must be positive");
+        int ndev = 0;
+        GL_CUDA(cudaGetDeviceCount(&ndev));
+        GL_REQUIRE(device >= 0 && device < ndev, "no such device");
+        GL_CUDA(cudaSetDevice(device));
+        *flops_per_s = fp64_probe(iters, reps, n_sm, ms);
+    });
+}
+
 int gl_geneo_eigenvalues(gl_ctx *c, double *lambda, int capacity, int *count) {
     return guard([&] {
         require_ctx(c);
@@ -1483,6 +1569,8 @@ int gl_batch_create(gl_batch **out, int n, gl_ctx *const *items, void *cuda_stre
             for (int i = 0; i < n; ++i) {
                 GL_REQUIRE(items[i], "null laminate");
                 GL_REQUIRE(items[i]->device == b->device, "all laminates of a batch must be on one device");
+                GL_REQUIRE(!items[i]->have_mesh || items[i]->m.element == 0,
+                           "the batched engine takes Q2 laminates only (not the serendipity element)");
                 for (int j = 0; j < i; ++j) GL_REQUIRE(items[j] != items[i], "a laminate appears twice in the batch");
                 b->items.push_back(items[i]);
                 b->item_streams.push_back(items[i]->stream);

@@ -58,6 +58,7 @@ class Laminate:
     theta: np.ndarray | None = None   # (nz, ny, nx) misalignment, rad
     node_dr: np.ndarray | None = None  # (NZ, NY, NX) through-thickness node offset (geometric wrinkle), mm
     elem_mat: np.ndarray | None = None  # (nz, ny, nx) material index overriding the layer's (edge resin strips)
+    element: int = 0               # 0: 27-node Q2 hexahedra; 1: 20-node serendipity hexahedra (same node grid)
     dir_dof: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     dir_val: np.ndarray = field(default_factory=lambda: np.zeros(0))
     traction: list = field(default_factory=list)   # [(face, (tx, ty, tz))] MPa, global axes

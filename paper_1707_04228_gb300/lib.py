@@ -36,14 +36,14 @@ class gl_mesh(C.Structure):
                 ("nlayers", C.c_int), ("layer_nel", C.c_void_p), ("layer_thick", C.c_void_p),
                 ("layer_mat", C.c_void_p), ("layer_angle_deg", C.c_void_p), ("geometry", C.c_int),
                 ("R_inner", C.c_double), ("limb_L", C.c_double), ("arc_deg", C.c_double),
-                ("theta_e", C.c_void_p), ("node_dr", C.c_void_p), ("elem_mat", C.c_void_p)]
+                ("theta_e", C.c_void_p), ("node_dr", C.c_void_p), ("elem_mat", C.c_void_p), ("element", C.c_int)]
 
 
 class gl_opts(C.Structure):
     _fields_ = [("px", C.c_int), ("py", C.c_int), ("pz", C.c_int), ("overlap", C.c_int), ("nev", C.c_int),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("resid_period", C.c_int),
                 ("tol", C.c_double), ("sigma", C.c_double), ("eig_iters", C.c_int),
-                ("factor_ws_bytes", C.c_double), ("eig_group_bytes", C.c_double)]
+                ("factor_ws_bytes", C.c_double), ("eig_group_bytes", C.c_double), ("fp32_update", C.c_int)]
 
 
 class gl_info(C.Structure):
@@ -83,6 +83,7 @@ SIGNATURES = {
     "gl_num_elems": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "gl_rhs": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gl_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(gl_info)]),
+    "gl_solve_increment": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(gl_info)]),
     "gl_stress": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_stress_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gl_apply_K": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -101,6 +102,8 @@ SIGNATURES = {
     "gl_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "gl_profile_read": (C.c_int, [C.c_void_p, C.POINTER(gl_profile_data)]),
     "gl_kernel_launches": (C.c_longlong, []),
+    "gl_fp64_peak_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -140,6 +143,15 @@ def _ptr(a):
 def _check(lib, rc):
     if rc != 0:
         raise GLError(rc, lib.gl_last_error().decode())
+
+
+def fp64_peak_probe(device=0, iters=4096, reps=20):
+    """Measured FP64 FMA rate of the device (gl_fp64_peak_probe):
+    returns (flops per second, SM count, timed milliseconds)."""
+    lib = load()
+    f, n, ms = C.c_double(), C.c_int(), C.c_double()
+    _check(lib, lib.gl_fp64_peak_probe(device, iters, reps, C.byref(f), C.byref(n), C.byref(ms)))
+    return f.value, n.value, ms.value
 
 
 class Solver:
@@ -198,7 +210,7 @@ class Solver:
                     limb_L=float(lam.limb_L), arc_deg=float(lam.arc_deg),
                     theta_e=None if theta is None else theta.ctypes.data,
                     node_dr=None if dr is None else dr.ctypes.data,
-                    elem_mat=None if em is None else em.ctypes.data)
+                    elem_mat=None if em is None else em.ctypes.data, element=int(getattr(lam, "element", 0)))
         _check(self.lib, self.lib.gl_set_mesh(self.ctx, C.byref(m)))
 
     def set_dirichlet(self, dof, val):
@@ -211,10 +223,11 @@ class Solver:
         _check(self.lib, self.lib.gl_set_traction(self.ctx, int(face), _ptr(tv)))
 
     def setup(self, px, py, pz, overlap=1, nev=8, tol=1e-10, max_iter=2000, precision=GL_PREC_FP64,
-              resid_period=50, sigma=0.0, eig_iters=0, factor_ws_bytes=0.0, eig_group_bytes=0.0):
+              resid_period=50, sigma=0.0, eig_iters=0, factor_ws_bytes=0.0, eig_group_bytes=0.0,
+              fp32_update=0):
         o = gl_opts(px=px, py=py, pz=pz, overlap=overlap, nev=nev, max_iter=max_iter, precision=precision,
                     resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters,
-                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes)
+                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes, fp32_update=fp32_update)
         _check(self.lib, self.lib.gl_setup(self.ctx, C.byref(o)))
 
     @classmethod
@@ -256,6 +269,15 @@ class Solver:
             _check(self.lib, rc)
         self.last_info = info.as_dict()
         return out, self.last_info
+
+    def solve_increment(self, g, out=None, check=True):
+        """gl_solve_increment: du with K_ff du_f = g_f and du = 0 on the Dirichlet DOFs."""
+        out = np.empty(self.n_dof) if out is None else out
+        info = gl_info()
+        rc = self.lib.gl_solve_increment(self.ctx, _ptr(g), _ptr(out), C.byref(info))
+        if check:
+            _check(self.lib, rc)
+        return out, info.as_dict()
 
     def stress(self, u, s33=None, t13=None):
         ne = self.n_elem
@@ -363,10 +385,11 @@ class Batch:
         _check(self.lib, self.lib.gl_batch_create(C.byref(self.b), len(self.solvers), C.cast(arr, C.c_void_p), sp))
 
     def setup(self, px=0, py=0, overlap=1, nev=8, tol=1e-10, max_iter=2000, precision=GL_PREC_FP64,
-              resid_period=50, sigma=0.0, eig_iters=0, factor_ws_bytes=0.0, eig_group_bytes=0.0):
+              resid_period=50, sigma=0.0, eig_iters=0, factor_ws_bytes=0.0, eig_group_bytes=0.0,
+              fp32_update=0):
         o = gl_opts(px=px, py=py, pz=1, overlap=overlap, nev=nev, max_iter=max_iter, precision=precision,
                     resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters,
-                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes)
+                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes, fp32_update=fp32_update)
         _check(self.lib, self.lib.gl_batch_setup(self.b, C.byref(o)))
 
     def grid(self):

@@ -55,22 +55,31 @@ def test_autograd_gradient_matches_oracle_adjoint(setup_case):
 
 
 def test_gradient_matches_central_differences(setup_case):
+    """50 misalignment parameters drawn with seed 4228 from the ply elements of
+    the patch: adjoint gradient against central differences with h = 1e-6 rad
+    to 1e-5 relative, every component.  Each perturbed state is reached by an
+    increment solve from u(theta0) and the difference of J is formed without
+    cancelling large terms (theta_central_differences), so the differences
+    resolve components far below the largest one; the floor of 1e-9 of the
+    largest component is only there for a component that happens to vanish.
+    Both are also compared with the oracle's direct-solve gradient."""
     lam, mesh, mask, s, torch = setup_case
-    from paper_1707_04228_gb300.autograd import pnorm, stress_of_theta
+    from paper_1707_04228_gb300.autograd import pnorm, stress_of_theta, theta_central_differences
     theta0 = torch.tensor(mesh.theta, dtype=torch.float64, device="cuda")
     m = torch.tensor(mask, device="cuda")
     th = theta0.clone().requires_grad_(True)
     J = pnorm(stress_of_theta(th, s), m, 8)
     J.backward()
     g = th.grad.cpu().numpy()
-    h = 1e-6
-    for e in np.argsort(-np.abs(g))[:3]:
-        tp, tm = theta0.clone(), theta0.clone()
-        tp[e] += h
-        tm[e] -= h
-        with torch.no_grad():
-            jp = pnorm(stress_of_theta(tp, s), m, 8).item()
-            jm = pnorm(stress_of_theta(tm, s), m, 8).item()
-        fd = (jp - jm) / (2 * h)
-        assert abs(fd - g[e]) <= 1e-5 * abs(g[e])
-    s.set_theta(theta0)
+    params = np.flatnonzero(inputs.wrinkle_patch_mask(lam))
+    elems = np.random.default_rng(4228).choice(params, 50, replace=False)
+    fd = np.array(theta_central_differences(s, lam.nx, lam.ny, theta0, elems, m, 8, 1e-6))
+    _, g_ref, _ = adjoint.gradient(fem.System(mesh), mask, 8)
+    floor = 1e-9 * np.abs(g).max()
+    err = np.abs(fd - g[elems])
+    print("adjoint vs fd: max abs", err.max(), "floor", floor,
+          "max rel above 1e-3 max|g|", np.max((err / np.abs(g[elems]))[np.abs(g[elems]) > 1e-3 * np.abs(g).max()]),
+          "| fd vs oracle max abs", np.abs(fd - g_ref[elems]).max(),
+          "| adjoint vs oracle max abs", np.abs(g[elems] - g_ref[elems]).max())
+    assert np.all(err <= 1e-5 * np.abs(g[elems]) + floor)
+    assert np.abs(fd - g_ref[elems]).max() <= 1e-5 * np.abs(g_ref).max()
