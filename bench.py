@@ -95,6 +95,13 @@ def workload(name):
         desc = ("paper_corner_120x60x77_q2: the 39-ply wrinkle-study geometry (R 22 mm, 10 mm limbs, 52 mm width, "
                 "0.24/0.015 mm plies/resin, sech^2 wrinkle of 0.62 mm), 13,559,865 DOF, 128 subdomains (32x4x1), "
                 "10 eigenvectors, mixed (FP32 local factors and sweeps), tol 1e-8")
+    elif name == "paper_corner_periodic":
+        lam = inputs.paper_corner(nsub=(32, 1, 1), periodic=True)
+        lam.precision = 1
+        lam.tol = 1e-8
+        desc = ("paper_corner_120x60x77_q2 with periodic width conditions (the 39-ply wrinkle study: R 22 mm, 10 mm "
+                "limbs, 52 mm width, sech^2 wrinkle of 0.62 mm), 13,559,865 DOF, 32 subdomains spanning the width, "
+                "10 eigenvectors, mixed (FP32 local factors and sweeps), tol 1e-8")
     elif name in ("corner_small", "corner_small_mixed"):
         lam = inputs.curved_corner(n_arc=24, n_limb=4, n_width=8, nel_layer=1, name="curved_corner_small",
                                    nsub=(8, 2, 1), nev=10)

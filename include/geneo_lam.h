@@ -98,6 +98,14 @@ typedef struct {
  *            and the other calls ignore what they hold on input, except
  *            gl_stress_noalloc, which reads u as given.  Not available in
  *            gl_batch_*.
+ *   periodic_width  1: periodic conditions across the width (Section 3, the
+ *            39-ply study), u(s, l = y[0], r) = u(s, l = y[ny], r): every node
+ *            of the last width plane is identified with its partner on the
+ *            first.  The last plane's entries of N-vectors are handled like
+ *            the serendipity centres above (not unknowns; returned equal to
+ *            the first plane's).  Needs py = 1 (every subdomain spans the
+ *            width), ny >= 2 and element 0; not available in gl_batch_*.
+ *            Tractions on the faces l = y[0], y[ny] do not apply.
  * Material axes: R = R_l(psi + theta_e) R_r(phi), psi the frame angle at the
  * element centre (0 on limb 1 and flat plates), C_e constant per element. */
 typedef struct {
@@ -114,6 +122,7 @@ typedef struct {
     const double *node_dr;
     const int *elem_mat;
     int element;               /* 0 Q2, 1 serendipity-20 */
+    int periodic_width;        /* 0 or 1 */
 } gl_mesh;
 
 /* Solver options.

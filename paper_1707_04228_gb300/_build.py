@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libgeneo_lam.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mesh.cu", "ku.cu", "factor.cu", "geneo.cu", "adjoint.cu", "failure.cu", "noalloc.cu", "syrk_tc.cu", "probe.cu", "serendipity.cu", "problem.cu", "solver.cu", "symbolic.cpp"]
+SOURCES = ["mesh.cu", "ku.cu", "factor.cu", "geneo.cu", "adjoint.cu", "failure.cu", "noalloc.cu", "syrk_tc.cu", "probe.cu", "slaves.cu", "problem.cu", "solver.cu", "symbolic.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -23,7 +23,7 @@
 
 #include "factor.h"
 #include "q2.cuh"
-#include "serendipity.h"
+#include "slaves.h"
 
 namespace gl {
 
@@ -859,6 +859,81 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict
         for (int r = 0; r < NR; ++r) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
 }
 
+// Backward substitution with per-column shuffle reductions, used for the FP32
+// factors: for each block B of 32 pivots from the last to the first, one
+// reduction down each column of the block over the rows from B to the end of
+// the front (the rows of B with +, the rows below with -); warp w owns the
+// columns w, w + 8, ..., its lanes stride the rows with 8 loads in flight, and
+// a shuffle tree adds the lanes.  Its adds cost little where the sweep is
+// bound by HBM (FP32), and its 32 registers and small shared memory keep many
+// CTAs and loads in flight; the FP64 sweep, bound by the FP64 pipe, uses k_bwd.
+template <class T, int NR>
+__global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd_shfl(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
+                                             const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
+                                             int kcols, int c0) {
+    extern __shared__ unsigned char smraw[];
+    const FrontDesc d = D[fronts[blockIdx.x]];
+    const int p = d.p, f = d.p + d.q, n = d.vlen;
+    T *v = reinterpret_cast<T *>(smraw);
+    T *red = v + (int64_t)f * NR;   // 32 x NR column results of the block
+    T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
+    for (int i = threadIdx.x; i < f; i += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            v[i + r * f] = i < p ? xs[(int64_t)r * n + d.first + i] : xs[(int64_t)r * n + rows[d.row_off + i]];
+    __syncthreads();
+    if (p == 0) return;
+    const T *Lp = L + d.l_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int jb = ((p - 1) / 32) * 32; jb >= 0; jb -= 32) {
+        const int kb = min(32, p - jb);
+        for (int j = warp; j < kb; j += nw) {
+            const T *col = Lp + (int64_t)(jb + j) * f;
+            T acc[NR];
+            {
+                // rows of B: L[B,B]^{-1}[i, j] y_i for i >= j, negated here and restored below
+                const bool in = lane >= j && lane < kb;
+                const T l = in ? col[jb + lane] : T(0);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = -(l * v[jb + (in ? lane : 0) + r * f]);
+            }
+            int i = jb + kb + lane;
+            // rows below B: + W[i, j] x_i, 8 independent loads per lane in flight
+            for (; i + 7 * 32 < f; i += 8 * 32) {
+                T l[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) l[t] = col[i + 32 * t];
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) acc[r] += l[t] * v[i + 32 * t + r * f];
+            }
+            for (; i < f; i += 32) {
+                const T l = col[i];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] += l * v[i + r * f];
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                T a = acc[r];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) red[j + 32 * r] = -a;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32 * NR) {
+            const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
+            if (j < kb) v[jb + j + r * f] = red[j + 32 * r];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
+}
+
+
 // Shared memory of the sweeps.  Forward: the front vector (f x NR) and the
 // copy of x_B (32 x NR), plus the static inverse block.  Backward: the front
 // vector, the partial column sums (NR x nw x 32) and one 32 x 33 tile per warp,
@@ -918,7 +993,13 @@ static void ensure_sweep_smem(int max_f) {
     raise_smem_limit(limit, SMEM_PER_CTA - sweep_static_smem<T, NR>(), [](size_t v) {
         GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
         GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
+        GL_CUDA(cudaFuncSetAttribute(k_bwd_shfl<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
     });
+}
+
+template <class T, int NR>
+static size_t bwd_shfl_dyn_smem(int f) {
+    return ((size_t)std::max(f, 1) + 32) * NR * sizeof(T);
 }
 
 void sweep_smem_for_plan(int max_f) {
@@ -944,9 +1025,17 @@ static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c
     for (int dpt = 0; dpt < nlev; ++dpt) {
         const Level &Lv = P.levels[dpt];
         if (Lv.fronts.empty()) continue;
-        const int nt = bwd_threads<T, NR>(Lv.max_f, Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256);
-        const size_t sm = bwd_dyn_smem<T, NR>(Lv.max_f, nt);
-        k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+        const int want = Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256;
+        if (sizeof(T) == 4) {
+            const size_t sm = bwd_shfl_dyn_smem<T, NR>(Lv.max_f);
+            k_bwd_shfl<T, NR><<<(unsigned)Lv.fronts.size(), want, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x,
+                                                                          kcols, c0);
+        } else {
+            const int nt = bwd_threads<T, NR>(Lv.max_f, want);
+            const size_t sm = bwd_dyn_smem<T, NR>(Lv.max_f, nt);
+            k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols,
+                                                                  c0);
+        }
     }
     GL_CUDA(cudaGetLastError());
 }

@@ -98,7 +98,8 @@ struct MeshHost {
     int nx = 0, ny = 0, nz = 0, NX = 0, NY = 0, NZ = 0;
     int64_t n_nodes = 0, n_dof = 0, n_elem = 0;
     int geometry = 0;
-    int element = 0;                         // 0 Q2 (27 nodes), 1 serendipity (20 nodes; serendipity.h)
+    int element = 0;                         // 0 Q2 (27 nodes), 1 serendipity (20 nodes; slaves.h)
+    bool periodic = false;                   // periodic width: plane iy = NY-1 identified with iy = 0 (slaves.h)
     double R_inner = 0, limb_L = 0, arc_rad = 0;
     std::vector<double> sv, lv, rv;          // vertex coordinates (rv = depth from inner face)
     std::vector<double> tn, ln, rn;          // Q2 node parameters

@@ -19,7 +19,7 @@
 // scaling on both sides, several vectors per call).
 #include "geneo.h"
 #include "q2.cuh"
-#include "serendipity.h"
+#include "slaves.h"
 
 namespace gl {
 

@@ -152,8 +152,9 @@ void problem_local_elems(const Problem &P, int s0, int s1, const FactorPlan &pla
                     elem.push_back((int)(pt.elem_off + ex + (int64_t)m.nx * (ey + (int64_t)m.ny * ez)));
                     sub.push_back(jl);
                     for (int a = 0; a < 27; ++a) {
-                        int x = 2 * ex + a % 3 - b.nbox[0], y = 2 * ey + (a / 3) % 3 - b.nbox[2],
-                            z = 2 * ez + a / 9 - b.nbox[4];
+                        int yg = 2 * ey + (a / 3) % 3;
+                        if (m.periodic && yg == m.NY - 1) yg = 0;   // the first-plane partner carries the DOFs
+                        int x = 2 * ex + a % 3 - b.nbox[0], y = yg - b.nbox[2], z = 2 * ez + a / 9 - b.nbox[4];
                         for (int cc = 0; cc < 3; ++cc)
                             loc.push_back(map[3 * ((size_t)x + (size_t)nbx * (y + (size_t)nby * z)) + cc]);
                     }

@@ -1,5 +1,11 @@
-// The 20-node serendipity hexahedron (Section 2.1: the paper's own element)
-// on the Q2 node grid.
+// DOFs of the Q2 node grid that are not unknowns but fixed combinations of
+// others ("slaves" of "masters"): the face and body centres of the 20-node
+// serendipity element, and the last width plane under periodic width
+// conditions.  Both constraints read u_Q2 = P u and wrap the Q2 kernels with a
+// fill (slaves from masters) before and the transpose fold (masters += P^T y,
+// slaves zeroed) after them.
+//
+// Serendipity (Section 2.1: the paper's own element) on the Q2 node grid.
 //
 // The serendipity space of an element is a subspace of its triquadratic Q2
 // space, and its 20 nodes are the Q2 nodes with at most one odd local index
@@ -18,7 +24,9 @@
 // node numbering, treats the slave DOFs as eliminated (zero in the solver),
 // and wraps the Q2 kernels: fill (u <- P u on the slave entries) before and
 // the transpose fold (masters += P^T y, slaves zeroed) after them.
-#include "serendipity.h"
+#include <algorithm>
+
+#include "slaves.h"
 
 namespace gl {
 
@@ -88,6 +96,63 @@ void s20_fill(const MeshHost &m, double *v, cudaStream_t s) {
 void s20_fold(const MeshHost &m, double *y, cudaStream_t s) {
     k_s20_fold<<<(unsigned)((m.n_nodes + 255) / 256), 256, 0, s>>>(m.NX, m.NY, m.NZ, y);
     GL_CUDA(cudaGetLastError());
+}
+
+// Periodic width conditions (Section 3, the 39-ply study: u(s, 0, r) =
+// u(s, W, r)): every node of the last width plane iy = NY - 1 is the slave
+// of its partner on the first plane iy = 0 (weight 1).  Only the unknowns are
+// identified; the nodes keep their own coordinates.
+__global__ void k_per_fill(int NX, int NY, int NZ, double *__restrict__ v) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)NX * NZ) return;
+    const int ix = (int)(t % NX), iz = (int)(t / NX);
+    const int64_t master = ix + (int64_t)NX * ((int64_t)NY * iz);
+    const int64_t slave = ix + (int64_t)NX * ((NY - 1) + (int64_t)NY * iz);
+    for (int c = 0; c < 3; ++c) v[3 * slave + c] = v[3 * master + c];
+}
+
+__global__ void k_per_fold(int NX, int NY, int NZ, double *__restrict__ y) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)NX * NZ) return;
+    const int ix = (int)(t % NX), iz = (int)(t / NX);
+    const int64_t master = ix + (int64_t)NX * ((int64_t)NY * iz);
+    const int64_t slave = ix + (int64_t)NX * ((NY - 1) + (int64_t)NY * iz);
+    for (int c = 0; c < 3; ++c) {
+        y[3 * master + c] += y[3 * slave + c];
+        y[3 * slave + c] = 0.0;
+    }
+}
+
+void slave_fill(const MeshHost &m, double *v, cudaStream_t s) {
+    if (m.element == 1) s20_fill(m, v, s);
+    if (m.periodic) {
+        const int64_t n = (int64_t)m.NX * m.NZ;
+        k_per_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.NX, m.NY, m.NZ, v);
+        GL_CUDA(cudaGetLastError());
+    }
+}
+
+void slave_fold(const MeshHost &m, double *y, cudaStream_t s) {
+    if (m.periodic) {
+        const int64_t n = (int64_t)m.NX * m.NZ;
+        k_per_fold<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m.NX, m.NY, m.NZ, y);
+        GL_CUDA(cudaGetLastError());
+    }
+    if (m.element == 1) s20_fold(m, y, s);
+}
+
+std::vector<int64_t> slave_dofs(const MeshHost &m) {
+    std::vector<int64_t> out;
+    if (m.element == 1) out = s20_slave_dofs(m);
+    if (m.periodic)
+        for (int iz = 0; iz < m.NZ; ++iz)
+            for (int ix = 0; ix < m.NX; ++ix) {
+                const int64_t n = ix + (int64_t)m.NX * ((m.NY - 1) + (int64_t)m.NY * iz);
+                for (int c = 0; c < 3; ++c) out.push_back(3 * n + c);
+            }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return out;
 }
 
 std::vector<int64_t> s20_slave_dofs(const MeshHost &m) {

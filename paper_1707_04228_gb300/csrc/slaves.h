@@ -1,6 +1,7 @@
-// The 20-node serendipity element as a constrained Q2 element (see
-// serendipity.cu): the 7 face/body-centre nodes of an element ("slaves") take
-// fixed combinations of the 20 serendipity nodes.
+// DOFs of the Q2 grid fixed by constraints (slaves.cu): the face/body centres
+// of the 20-node serendipity element (fixed combinations of the element's 20
+// nodes) and the last width plane under periodic width conditions (equal to
+// the first plane).
 #pragma once
 
 #include "gl_internal.h"
@@ -36,5 +37,13 @@ void s20_fill(const MeshHost &m, double *v, cudaStream_t s);
 void s20_fold(const MeshHost &m, double *y, cudaStream_t s);
 // DOFs of the slave nodes (eliminated from the serendipity system).
 std::vector<int64_t> s20_slave_dofs(const MeshHost &m);
+
+// Every constraint of the mesh (serendipity and/or periodic width), in the
+// order that composes them: fill = periodic after serendipity, fold the
+// reverse.  slave_dofs: all slave DOFs, sorted.
+inline bool has_slaves(const MeshHost &m) { return m.element == 1 || m.periodic; }
+void slave_fill(const MeshHost &m, double *v, cudaStream_t s);
+void slave_fold(const MeshHost &m, double *y, cudaStream_t s);
+std::vector<int64_t> slave_dofs(const MeshHost &m);
 
 }  // namespace gl

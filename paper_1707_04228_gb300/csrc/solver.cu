@@ -17,7 +17,7 @@
 #include <thread>
 
 #include "problem.h"
-#include "serendipity.h"
+#include "slaves.h"
 
 namespace gl {
 
@@ -245,7 +245,7 @@ void build_geometry(gl_ctx *c) {
     c->d_ftrac.alloc(m.n_dof);
     c->d_ftrac.zero(s);
     for (auto &t : c->tractions) launch_traction(m, c->d_X.p, t.first, t.second.data(), c->d_ftrac.p, s);
-    if (m.element == 1) s20_fold(m, c->d_ftrac.p, s);            // f_20 = P^T f_Q2
+    if (has_slaves(m)) slave_fold(m, c->d_ftrac.p, s);            // f = P^T f_Q2
     GL_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -282,12 +282,13 @@ int64_t factor_solve_launches(const FactorPlan &P) {
 
 void apply_K(gl_ctx *c, const double *x, double *y) {
     prof_begin(c, PH_KU);
-    if (c->m.element == 1) {
-        // serendipity: y = P^T K_Q2 P x (slave entries of x filled in a copy, folded out of y)
+    if (has_slaves(c->m)) {
+        // constrained DOFs (serendipity, periodic width): y = P^T K_Q2 P x, the slave entries of x
+        // filled in a copy and folded out of y
         GL_CUDA(cudaMemcpyAsync(c->ks.p, x, c->m.n_dof * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        s20_fill(c->m, c->ks.p, c->stream);
+        slave_fill(c->m, c->ks.p, c->stream);
         launch_ku(c->m, c->d_C.p, c->d_geo.p, c->ks.p, y, c->stream);
-        s20_fold(c->m, y, c->stream);
+        slave_fold(c->m, y, c->stream);
         g_launches += 2;
     } else {
         launch_ku(c->m, c->d_C.p, c->d_geo.p, x, y, c->stream);
@@ -340,6 +341,7 @@ void setup(gl_ctx *c, const gl_opts &o) {
     GL_REQUIRE(o.overlap >= 1, "overlap must be >= 1");
     GL_REQUIRE(o.nev >= 0 && o.nev <= 28, "nev must be in [0, 28]");
     GL_REQUIRE(o.px <= c->m.nx && o.py <= c->m.ny && o.pz <= c->m.nz, "more subdomains than elements along an axis");
+    GL_REQUIRE(!c->m.periodic || o.py == 1, "periodic width needs py = 1 (subdomains spanning the width)");
     GL_REQUIRE(o.precision == GL_PREC_FP64 || o.precision == GL_PREC_MIXED, "unknown precision mode");
     GL_REQUIRE(o.fp32_update == 0 || o.fp32_update == 1, "fp32_update must be 0 or 1");
     c->ready = false;
@@ -359,13 +361,13 @@ void setup(gl_ctx *c, const gl_opts &o) {
     std::vector<uint8_t> is_dir(m.n_dof, 0);
     for (int64_t d : c->dir_dof) is_dir[d] = 1;
     {
-        // the solver's eliminated DOFs: the prescribed ones with their values, and for the
-        // serendipity element the slave entries with 0 (a prescribed value there is ignored:
-        // the serendipity field fixes it)
+        // the solver's eliminated DOFs: the prescribed ones with their values, and the slave
+        // entries (serendipity centres, the periodic width plane) with 0 (a prescribed value
+        // there is ignored: the constraint fixes it)
         std::vector<int64_t> dd(c->dir_dof);
         std::vector<double> dv(c->dir_val);
-        if (m.element == 1) {
-            std::vector<int64_t> sl = s20_slave_dofs(m);
+        if (has_slaves(m)) {
+            std::vector<int64_t> sl = slave_dofs(m);
             std::vector<uint8_t> is_slave(m.n_dof, 0);
             for (int64_t d : sl) is_slave[d] = 1;
             dd.clear();
@@ -453,7 +455,7 @@ void setup(gl_ctx *c, const gl_opts &o) {
         std::fprintf(stderr, "[gl]   %d dependent coarse columns dropped\n", c->co.n_dropped);
     // work vectors
     const int64_t N = m.n_dof;
-    if (m.element == 1) c->ks.alloc(N);
+    if (has_slaves(m)) c->ks.alloc(N);
     else c->ks.release();
     for (DBuf<double> *b : {&c->x, &c->r, &c->z, &c->p, &c->q, &c->ud, &c->fe}) b->alloc(N);
     c->partials.alloc(1024);
@@ -589,8 +591,8 @@ void solve(gl_ctx *c, const double *f, double *u, gl_info *info, bool homogeneou
     const double rt = read_scalar(c, &S->rr);
     axpy(c->x.p, 1.0, c->ud.p, N, s);
     g_launches += nds + 4;
-    if (c->m.element == 1) {
-        s20_fill(c->m, c->x.p, s);   // the serendipity field's values on the face and body centres
+    if (has_slaves(c->m)) {
+        slave_fill(c->m, c->x.p, s);   // the constrained entries carry the field's values
         g_launches += 1;
     }
     for (int ph = 0; ph < PH_N; ++ph) prof_fold(c, ph);
@@ -1141,6 +1143,9 @@ int gl_set_mesh(gl_ctx *c, const gl_mesh *mesh) {
         GL_REQUIRE(mesh->nx >= 1 && mesh->ny >= 1 && mesh->nlayers >= 1, "empty mesh");
         GL_REQUIRE(mesh->geometry == 0 || mesh->geometry == 1, "geometry must be 0 or 1");
         GL_REQUIRE(mesh->element == 0 || mesh->element == 1, "element must be 0 (Q2) or 1 (serendipity)");
+        GL_REQUIRE(mesh->periodic_width == 0 || mesh->periodic_width == 1, "periodic_width must be 0 or 1");
+        GL_REQUIRE(!mesh->periodic_width || (mesh->element == 0 && mesh->ny >= 2),
+                   "periodic width needs the Q2 element and at least 2 elements across the width");
         MeshHost m;
         m.nx = mesh->nx;
         m.ny = mesh->ny;
@@ -1174,6 +1179,7 @@ int gl_set_mesh(gl_ctx *c, const gl_mesh *mesh) {
         GL_REQUIRE(m.n_dof < (int64_t)1 << 31, "mesh too large for 32-bit local indices");
         m.geometry = mesh->geometry;
         m.element = mesh->element;
+        m.periodic = mesh->periodic_width != 0;
         m.R_inner = mesh->R_inner;
         m.limb_L = mesh->limb_L;
         m.arc_rad = mesh->arc_deg * M_PI / 180.0;
@@ -1311,7 +1317,7 @@ int gl_stress(gl_ctx *c, const double *u, double *s33, double *t13, double *peak
         DBuf<double> du, d33, d13, dpk;
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
-        if (m.element == 1) s20_fill(m, du.p, s);
+        if (has_slaves(m)) slave_fill(m, du.p, s);
         d33.alloc(m.n_elem);
         d13.alloc(m.n_elem);
         launch_stress(m, c->d_X.p, c->d_C.p, c->d_psi.p, du.p, d33.p, d13.p, s);
@@ -1396,7 +1402,7 @@ int gl_failure_index(gl_ctx *c, const double *u, double s33_allow, double s13_al
         DBuf<unsigned long long> best;
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
-        if (m.element == 1) s20_fill(m, du.p, s);
+        if (has_slaves(m)) slave_fill(m, du.p, s);
         dF.alloc(m.n_elem);
         best.alloc(1);
         launch_failure(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_resin.p, du.p, s33_allow, s13_allow, dF.p, best.p, s);
@@ -1438,7 +1444,7 @@ int gl_stress_vjp(gl_ctx *c, const double *u, const double *w33, const double *w
         DBuf<double> du, d33, d13, dgu, dgt;
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
-        if (m.element == 1) s20_fill(m, du.p, s);
+        if (has_slaves(m)) slave_fill(m, du.p, s);
         if (w33) {
             d33.alloc(m.n_elem);
             to_device(d33.p, w33, m.n_elem, s);
@@ -1455,7 +1461,7 @@ int gl_stress_vjp(gl_ctx *c, const double *u, const double *w33, const double *w
         launch_stress_vjp(m, c->d_X.p, c->d_C.p, c->d_psi.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
                           c->d_layer_angle.p, c->d_theta.p, c->d_matC.p, du.p, d33.p, d13.p, dgu.p, dgt.p, s);
         g_launches += 1;
-        if (dJdu && m.element == 1) s20_fold(m, dgu.p, s);   // dJ/du_20 = P^T dJ/du_Q2
+        if (dJdu && has_slaves(m)) slave_fold(m, dgu.p, s);   // dJ/du = P^T dJ/du_Q2
         if (dJdu) from_device(dJdu, dgu.p, m.n_dof, s);
         if (dJdth) from_device(dJdth, dgt.p, m.n_elem, s);
         GL_CUDA(cudaStreamSynchronize(s));
@@ -1474,7 +1480,7 @@ int gl_adjoint(gl_ctx *c, const double *u, const double *dJdu, double *grad, gl_
         solve(c, dJdu, lam.p, info, true);          // K_ff lambda = (dJ/du)_f, lambda = 0 on Dirichlet DOFs
         du.alloc(m.n_dof);
         to_device(du.p, u, m.n_dof, s);
-        if (m.element == 1) s20_fill(m, du.p, s);   // lambda comes back filled from solve()
+        if (has_slaves(m)) slave_fill(m, du.p, s);   // lambda comes back filled from solve()
         dg.alloc(m.n_elem);
         launch_adjoint_contract(m, c->d_geo.p, c->d_layer_of_ez.p, c->d_layer_mat.p, c->d_elem_mat.p,
                                 c->d_layer_angle.p,
@@ -1569,8 +1575,8 @@ int gl_batch_create(gl_batch **out, int n, gl_ctx *const *items, void *cuda_stre
             for (int i = 0; i < n; ++i) {
                 GL_REQUIRE(items[i], "null laminate");
                 GL_REQUIRE(items[i]->device == b->device, "all laminates of a batch must be on one device");
-                GL_REQUIRE(!items[i]->have_mesh || items[i]->m.element == 0,
-                           "the batched engine takes Q2 laminates only (not the serendipity element)");
+                GL_REQUIRE(!items[i]->have_mesh || (items[i]->m.element == 0 && !items[i]->m.periodic),
+                           "the batched engine takes Q2 laminates without periodic width conditions only");
                 for (int j = 0; j < i; ++j) GL_REQUIRE(items[j] != items[i], "a laminate appears twice in the batch");
                 b->items.push_back(items[i]);
                 b->item_streams.push_back(items[i]->stream);

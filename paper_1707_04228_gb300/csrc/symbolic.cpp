@@ -12,6 +12,13 @@
 // subtree region, i.e. the enclosing box of all elements touching the region
 // minus the region itself (all of them lie on ancestor separators).  The
 // front of a supernode = its pivots followed by its structure rows.
+//
+// Periodic width (the last width plane identified with the first; the
+// subdomain then spans the width): the first plane is the root separator, a
+// supernode with one child, the rest of the box below it dissected as usual.
+// Wherever a node of the last plane appears -- in a region's neighbourhood or
+// among an element's nodes -- its partner on the first plane stands for it,
+// and the root also assembles the elements of the last width layer.
 #include <algorithm>
 #include <cstdio>
 
@@ -56,6 +63,8 @@ struct Builder {
                    ((int64_t)(y - active.lo[1]) + (int64_t)(active.hi[1] - active.lo[1] + 1) * (z - active.lo[2]));
     }
     int64_t gnode(int x, int y, int z) const { return (int64_t)x + (int64_t)m.NX * ((int64_t)y + (int64_t)m.NY * z); }
+    // the node that carries the DOFs of (x, y, z): its first-plane partner on the last width plane
+    int wrap_y(int y) const { return (m.periodic && y == m.NY - 1) ? 0 : y; }
 
     // numbers the active DOFs of the nodes of box b (x fastest), returns count
     int number_box(const Box &b) {
@@ -163,7 +172,18 @@ void build_symbolic(const MeshHost &m, const SubBox &b, const std::vector<uint8_
     }
     if (A.count() <= 0) fail(GL_ERR_INVALID_ARG, "empty subdomain");
     Builder B(m, dof_is_dir, A, leaf_nodes, S);
-    B.nd(A, 0);
+    const bool wrap = m.periodic;
+    if (wrap) {
+        if (A.lo[1] != 0 || A.hi[1] != m.NY - 1) fail(GL_ERR_INVALID_ARG, "periodic width: a subdomain must span the width");
+        Box P = A, Rr = A;
+        P.hi[1] = 0;
+        Rr.lo[1] = 1;
+        const int c0 = B.nd(Rr, 1);
+        const int root = B.new_supernode(A, P, 0, c0, -1);
+        (void)root;
+    } else {
+        B.nd(A, 0);
+    }
     S.n = B.next_local;
 
     // structure rows
@@ -176,12 +196,14 @@ void build_symbolic(const MeshHost &m, const SubBox &b, const std::vector<uint8_
         for (int z = E.lo[2]; z <= E.hi[2]; ++z)
             for (int y = E.lo[1]; y <= E.hi[1]; ++y)
                 for (int x = E.lo[0]; x <= E.hi[0]; ++x) {
-                    if (Builder::inside(R, x, y, z)) continue;
-                    int64_t li = B.lidx(x, y, z);
+                    const int yw = B.wrap_y(y);
+                    if (Builder::inside(R, x, yw, z)) continue;
+                    int64_t li = B.lidx(x, yw, z);
                     int f = B.node_first[li];
                     for (int k = 0; k < B.node_ndof[li]; ++k) rows.push_back(f + k);
                 }
         std::sort(rows.begin(), rows.end());
+        rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
         Supernode &s = S.sn[i];
         if (!rows.empty() && rows.front() < s.first + s.p)
             fail(GL_ERR_STATE, "symbolic: structure row precedes its supernode");
@@ -237,13 +259,18 @@ void build_symbolic(const MeshHost &m, const SubBox &b, const std::vector<uint8_
             ehi[d] = std::min(P.hi[d] / 2, eb_hi[d] - 1);
         }
         const std::vector<int> &st = structs[i];
+        // element rows of the width to visit: those touching the pivots, and under periodic width
+        // the last row for a pivot box on the first plane (its last-plane nodes stand for them)
+        std::vector<int> eys;
+        for (int ey = elo[1]; ey <= ehi[1]; ++ey) eys.push_back(ey);
+        if (wrap && P.lo[1] == 0 && eb_hi[1] - 1 > ehi[1]) eys.push_back(eb_hi[1] - 1);
         for (int ez = elo[2]; ez <= ehi[2]; ++ez)
-            for (int ey = elo[1]; ey <= ehi[1]; ++ey)
+            for (int ey : eys)
                 for (int ex = elo[0]; ex <= ehi[0]; ++ex) {
                     int16_t pos[81];
                     bool any_pivot = false;
                     for (int a = 0; a < 27; ++a) {
-                        int x = 2 * ex + a % 3, y = 2 * ey + (a / 3) % 3, z = 2 * ez + a / 9;
+                        int x = 2 * ex + a % 3, y = B.wrap_y(2 * ey + (a / 3) % 3), z = 2 * ez + a / 9;
                         bool act = Builder::inside(A, x, y, z);
                         int64_t li = act ? B.lidx(x, y, z) : 0;
                         uint8_t mask = act ? B.node_comp_mask[li] : 0;

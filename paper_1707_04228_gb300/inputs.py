@@ -59,6 +59,7 @@ class Laminate:
     node_dr: np.ndarray | None = None  # (NZ, NY, NX) through-thickness node offset (geometric wrinkle), mm
     elem_mat: np.ndarray | None = None  # (nz, ny, nx) material index overriding the layer's (edge resin strips)
     element: int = 0               # 0: 27-node Q2 hexahedra; 1: 20-node serendipity hexahedra (same node grid)
+    periodic_width: int = 0        # 1: u equal on the width planes l = lv[0] and l = lv[-1]
     dir_dof: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     dir_val: np.ndarray = field(default_factory=lambda: np.zeros(0))
     traction: list = field(default_factory=list)   # [(face, (tx, ty, tz))] MPa, global axes
@@ -385,7 +386,7 @@ PAPER_39_PLY = ([-45, 45, 90, 0] * 2 + [-45, 45] * 2 + [90, -45, 45, 90, 0, -45,
 
 
 def paper_corner(n_arc=100, n_limb=10, n_width=60, d_wrinkle=0.62, delta=-1e-3, limb_bias=3.0,
-                 nsub=(32, 4, 1), nev=10, edge_resin=0.0, n_edge=2, name=None) -> Laminate:
+                 nsub=(32, 4, 1), nev=10, edge_resin=0.0, n_edge=2, periodic=False, name=None) -> Laminate:
     """The geometry of the paper's 39-ply wrinkle study (Section 3): inner radius
     22 mm, 10 mm limbs, 52 mm width, 0.24 mm plies with 0.015 mm resin
     interfaces (T = 9.93 mm), the printed stacking sequence, one Q2 element
@@ -395,8 +396,11 @@ def paper_corner(n_arc=100, n_limb=10, n_width=60, d_wrinkle=0.62, delta=-1e-3, 
     Loads as for the other corners: limb 1 clamped, a rigid opening rotation
     of limb 2's end.  edge_resin > 0 adds the paper's resin strips of that
     width (mm, n_edge elements each) along both free edges of the width (all
-    layers resin there); the periodic width conditions are not modelled.
-    Default mesh 120 x 60 x 77 elements, 13,559,865 DOF."""
+    layers resin there); periodic=True applies the study's periodic width
+    conditions instead (no free edges; one subdomain across the width, so
+    nsub[1] is set to 1; the wrinkle is symmetric about mid-width, so the two
+    width faces have the same shape).  Default mesh 120 x 60 x 77 elements,
+    13,559,865 DOF."""
     assert len(PAPER_39_PLY) == 39
     nel, th, mat, ang = _stack_with_resin(PAPER_39_PLY, 0.24, 0.015, 1, 1)
     limb1 = graded(n_limb, -1.0, 0.0, limb_bias, fine_at_b=True) if n_limb else np.array([0.0])
@@ -420,6 +424,10 @@ def paper_corner(n_arc=100, n_limb=10, n_width=60, d_wrinkle=0.62, delta=-1e-3, 
     if d_wrinkle:
         lam.node_dr, lam.theta = sech2_wrinkle(lam, d_wrinkle, width=52.0)
     lam.dir_dof, lam.dir_val = merge_dirichlet(clamp_face(lam, FACE_SM), limb_end_rotation(lam, delta))
+    if periodic:
+        assert edge_resin == 0, "periodic width conditions leave no free edge for resin strips"
+        lam.periodic_width = 1
+        lam.py = 1
     return lam
 
 

@@ -36,7 +36,8 @@ class gl_mesh(C.Structure):
                 ("nlayers", C.c_int), ("layer_nel", C.c_void_p), ("layer_thick", C.c_void_p),
                 ("layer_mat", C.c_void_p), ("layer_angle_deg", C.c_void_p), ("geometry", C.c_int),
                 ("R_inner", C.c_double), ("limb_L", C.c_double), ("arc_deg", C.c_double),
-                ("theta_e", C.c_void_p), ("node_dr", C.c_void_p), ("elem_mat", C.c_void_p), ("element", C.c_int)]
+                ("theta_e", C.c_void_p), ("node_dr", C.c_void_p), ("elem_mat", C.c_void_p), ("element", C.c_int),
+                ("periodic_width", C.c_int)]
 
 
 class gl_opts(C.Structure):
@@ -210,7 +211,8 @@ class Solver:
                     limb_L=float(lam.limb_L), arc_deg=float(lam.arc_deg),
                     theta_e=None if theta is None else theta.ctypes.data,
                     node_dr=None if dr is None else dr.ctypes.data,
-                    elem_mat=None if em is None else em.ctypes.data, element=int(getattr(lam, "element", 0)))
+                    elem_mat=None if em is None else em.ctypes.data, element=int(getattr(lam, "element", 0)),
+                    periodic_width=int(getattr(lam, "periodic_width", 0)))
         _check(self.lib, self.lib.gl_set_mesh(self.ctx, C.byref(m)))
 
     def set_dirichlet(self, dof, val):
