@@ -377,6 +377,9 @@ def main():
     ap.add_argument("--fp32-update", type=int, default=0, choices=[0, 1],
                     help="mixed precision: trailing updates of the FP32 factors on the tensor cores (0) or the "
                          "FP32 CUDA cores (1)")
+    ap.add_argument("--sweep-overlap", type=int, default=0,
+                    help="local solves: overlap the sweeps of two halves of the subdomains, their top N levels "
+                         "on a high-priority stream (0: the library default, -1: sequential)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="after a mixed-precision run, solve the same laminate in FP64 and report the differences")
     args = ap.parse_args()
@@ -414,7 +417,7 @@ def main():
     t0 = time.perf_counter()
     prec = getattr(lam, "precision", 0)
     s = lib.Solver.from_laminate(lam, device=local_rank, precision=prec, max_iter=5000,
-                                 fp32_update=args.fp32_update)
+                                 fp32_update=args.fp32_update, sweep_overlap=args.sweep_overlap)
     setup_s = time.perf_counter() - t0
     N, NE = s.n_dof, s.n_elem
     dev = torch.device("cuda", local_rank)
@@ -472,6 +475,7 @@ def main():
     s.profile(True)
     s.solve(f, out=u)
     prof = s.profile_read()
+    lv = s.profile_levels()
     s.profile(False)
     hbm, hbm_src = peaks()
     # algorithmic work of one local-solve phase: every nonzero of the lower-triangular
@@ -498,6 +502,21 @@ def main():
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
                 "kernel": "local forward/backward supernodal sweeps (all levels) + gather/scatter",
                 "peak_note": f"HBM {hbm_src}"}
+    # per dissection level: sweep times per application and their rate (FP64: FMA pipe; FP32: HBM)
+    nc = max(lv["calls"], 1)
+    levels = {"fronts": lv["fronts"].tolist(), "nonzeros": lv["nonzeros"].tolist(),
+              "padded_entries": lv["padded"].tolist(), "max_front": lv["max_front"].tolist(),
+              "fwd_us": [round(1e3 * t / nc, 1) for t in lv["fwd_ms"]],
+              "bwd_us": [round(1e3 * t / nc, 1) for t in lv["bwd_ms"]]}
+    for k in ("fwd", "bwd"):
+        ms_k = lv[k + "_ms"] / nc
+        if fp64:
+            rate = [2 * z / (t / 1e3) / 1e12 / FP64_PEAK_TFLOPS if t > 0 else 0.0
+                    for z, t in zip(lv["nonzeros"], ms_k)]
+        else:
+            rate = [z * bpe / (t / 1e3) / 1e9 / hbm if t > 0 else 0.0 for z, t in zip(lv["nonzeros"], ms_k)]
+        levels[k + "_frac"] = [round(r, 3) for r in rate]
+    levels["frac_of"] = "measured FP64 FMA peak" if fp64 else "measured HBM copy bandwidth"
     ku = {"hbm_gbs": ku_bytes / (ku_ms / 1e3) / 1e9, "hbm_frac": ku_bytes / (ku_ms / 1e3) / 1e9 / hbm,
           "fp64_tflops": ku_flops / (ku_ms / 1e3) / 1e12,
           "fp64_frac": ku_flops / (ku_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "ms": ku_ms,
@@ -534,8 +553,11 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": desc, "l2": "inputs larger than L2 (local factors of "
                            f"{fe * bpe / 1e9:.1f} GB stream every iteration)",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roof, "ku": ku, "per_iteration": per_iter, "cpu_baseline": cpu, "e2e": e2e,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "stop": ("recurrence residual ||r||/||f|| <= tol; the FP64 true residual "
+                                    "||f - K u||/||f|| is reported as rel_resid_true" if prec == 0 else
+                                    "FP64 true residual ||f - K u||/||f|| <= tol")},
+                "roofline": roof, "ku": ku, "per_iteration": per_iter, "levels": levels, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(), "fp64_probe": probe, "gpu_launches": launches, "setup_s": setup_s,
                 "iters_per_solve": iters / max(args.steps, 1), "rel_resid_true": info["rel_resid_true"],
                 "n_free": info["n_free"], "factor_nonzeros": fe, "n_coarse": info["n_coarse"]}

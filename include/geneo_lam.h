@@ -157,13 +157,25 @@ typedef struct {
  *              its trailing matrices.  0 (default): 128-column panels whose
  *              rank-128 trailing updates run on the tensor cores (tcgen05,
  *              TF32 inputs split hi + lo, FP32 accumulation: FP32-level
- *              accuracy); 1: rank-32 updates on the FP32 CUDA cores. */
+ *              accuracy); 1: rank-32 updates on the FP32 CUDA cores.
+ *   sweep_overlap  how the triangular solves of the PCG iteration are
+ *              scheduled.  The subdomains are split in two halves whose
+ *              sweeps overlap: the second half starts when the first reaches
+ *              its top sweep_overlap dissection levels, and those levels of
+ *              either half run on a high-priority stream, so that one half's
+ *              many small deep fronts fill the SMs that the other half's few
+ *              large top fronts leave idle.  0 selects the default, every
+ *              level counted as top (the halves sweep concurrently, both at
+ *              high priority); < 0 sweeps sequentially.  Same arithmetic
+ *              either way.  Single laminates (gl_setup) only; timed phases
+ *              (gl_profile) sweep sequentially. */
 typedef struct {
     int px, py, pz, overlap, nev, max_iter, precision, resid_period;
     double tol, sigma;
     int eig_iters;
     double factor_ws_bytes, eig_group_bytes;
     int fp32_update;
+    int sweep_overlap;
 } gl_opts;
 
 /* Results of one solve.  rel_resid_true = ||f - K u||_2 / ||f||_2 on the
@@ -368,6 +380,23 @@ typedef struct {
 } gl_profile_data;
 int gl_profile(gl_ctx *ctx, int enable);
 int gl_profile_read(gl_ctx *ctx, gl_profile_data *out);
+/* Per dissection level of the local solves (Section 2.3), from the
+ * preconditioner applications timed since gl_profile(ctx, 1) (CUDA events
+ * before every level's launch; each timed application waits for its last
+ * launch).  For every depth d < min(max_levels, *n_levels): fwd_ms[d] and
+ * bwd_ms[d], the summed milliseconds of that level's forward and backward
+ * sweep launches; fronts[d], its fronts over all subdomains; nonzeros[d],
+ * their factor entries (sum of p(p+1)/2 + p q, what each sweep reads and
+ * multiplies once); padded[d], the entries of the 32-column block panels
+ * the kernels multiply (sum over blocks of 32 x the rows from the block
+ * down: the diagonal blocks' upper triangles and the last block's missing
+ * columns count as zeros); max_front[d], the rows of its largest front.
+ * *n_levels = number of levels, *calls = timed
+ * applications.  Every output pointer is host memory and may be NULL.
+ * Errors: GL_ERR_STATE before gl_setup, GL_ERR_INVALID_ARG for
+ * max_levels < 0. */
+int gl_profile_levels(gl_ctx *ctx, int max_levels, double *fwd_ms, double *bwd_ms, int64_t *fronts,
+                      int64_t *nonzeros, int64_t *padded, int *max_front, int *n_levels, int64_t *calls);
 long long gl_kernel_launches(void);
 
 /* FP64 FMA throughput of device `device`, measured: every thread of 8 blocks

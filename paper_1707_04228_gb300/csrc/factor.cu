@@ -108,6 +108,11 @@ void build_plan(const std::vector<SubSymbolic> &subs, FactorPlan &P, cudaStream_
         L.d_child[0].upload(L.child_slot[0], s);
         L.d_child[1].upload(L.child_slot[1], s);
     }
+    // the first half of the subdomains: fronts are listed per level in subdomain order
+    P.half_fronts.assign(P.levels.size(), 0);
+    for (size_t d = 0; d < P.levels.size(); ++d)
+        for (int g : P.levels[d].fronts)
+            if (P.fr[g].sub < P.n_sub / 2) ++P.half_fronts[d];
     P.d_fr.upload(P.fr, s);
     P.d_rows.upload(rows, s);
     P.d_rel.upload(rel, s);
@@ -643,135 +648,249 @@ template void numeric_factor<float>(FactorPlan &, const double *, const double *
 // over rows and columns with the block size, so either works.
 constexpr int SWEEP_MAX_THREADS = 512;
 constexpr int SWEEP_WIDE_BELOW = 1216;  // fronts per level
+// Threads per CTA of the sweeps on levels with at least SWEEP_WIDE_BELOW fronts
+// (SMALL: those whose largest front has at most SWEEP_SMALL_F rows).
+#ifndef GL_SWEEP_FWD_THREADS
+#define GL_SWEEP_FWD_THREADS 256
+#endif
+#ifndef GL_SWEEP_BWD_THREADS
+#define GL_SWEEP_BWD_THREADS 256
+#endif
+#ifndef GL_SWEEP_FWD_SMALL_THREADS
+#define GL_SWEEP_FWD_SMALL_THREADS 256
+#endif
+#ifndef GL_SWEEP_BWD_SMALL_THREADS
+#define GL_SWEEP_BWD_SMALL_THREADS 128
+#endif
+#ifndef GL_SWEEP_SMALL_F
+#define GL_SWEEP_SMALL_F 800
+#endif
+// The forward sweep of FP64 (FP32) factors treats the structure rows after the
+// triangle when GL_FWD_SPLIT64 (GL_FWD_SPLIT32) is 1, block by block otherwise.
+#ifndef GL_FWD_SPLIT64
+#define GL_FWD_SPLIT64 0
+#endif
+#ifndef GL_FWD_SPLIT32
+#define GL_FWD_SPLIT32 1
+#endif
+template <class T>
+constexpr bool fwd_split() {
+    return sizeof(T) == 8 ? GL_FWD_SPLIT64 != 0 : GL_FWD_SPLIT32 != 0;
+}
 
 // The sweeps read the partitioned-inverse form written by k_block_inverse.
-// Dynamic shared memory of both: the front's dense vector v (f x NR entries)
-// followed by a 32 x NR staging area (placed there, aliasing v's buffer, so
-// that its reads are not hoisted into registers).
+// Dynamic shared memory of both starts with the front's dense vector v
+// (f x NR entries).
 //
-// Forward substitution for the fronts of one level, one CTA per front: for
-// each block B of 32 pivots in turn, x_B is copied and L[B,B]^{-1} staged in
-// shared memory; warp 0 forms y_B = L[B,B]^{-1} x_B while all warps update the
-// rows below, x_i -= W[i,B] x_B, one row per thread.  No serial triangular
-// solve remains.  Structure rows are added into the ancestors' entries
-// atomically (siblings share rows).
+// Forward substitution for the fronts of one level, one CTA per front.  The
+// panel of a front is its pivot rows (the triangle, in partitioned-inverse
+// form) over its structure rows (a q x p rectangle).
+//   1. the triangle, block by block: x_B (the pivot values as left by the
+//      earlier blocks) is kept in X; the block's own rows hold
+//      L[B,B]^{-1} (zero above the diagonal), so they get y_B = L[B,B]^{-1} x_B,
+//      and the later pivot rows x_i -= W[i,B] x_B -- one row per thread, the
+//      block's rows one more row group.
+//   2. the rectangle at once: structure row i gets -sum_c W[i, c] X_c over all
+//      pivot columns c, one row per thread with no block barrier, and is added
+//      into the ancestors' entries atomically (siblings share rows).
+// One FMA per stored entry; no serial triangular solve remains.
 template <class T, int NR>
+__device__ __forceinline__ void fwd_row(const T *__restrict__ col0, int64_t ld, int i, int kb, const T *xb, int xs,
+                                        T acc[NR]) {
+    // acc[r] = sum over the kb columns of the block at col0 of W[i, j] xb[j + r xs]
+    if (kb == 32 && NR == 1) {
+        T l[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) l[j] = col0[i + (int64_t)j * ld];
+        T a0 = T(0), a1 = T(0);
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            a0 += l[j] * xb[j];
+            a1 += l[j + 1] * xb[j + 1];
+        }
+        acc[0] = a0 + a1;
+    } else if (kb == 32) {
+        // several right-hand sides: the row's loads in four groups of eight
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = T(0);
+#pragma unroll
+        for (int jc = 0; jc < 32; jc += 8) {
+            T l[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) l[j] = col0[i + (int64_t)(jc + j) * ld];
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[r] += l[j] * xb[jc + j + r * xs];
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = T(0);
+        for (int j = 0; j < kb; ++j) {
+            const T l = col0[i + (int64_t)j * ld];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] += l * xb[j + r * xs];
+        }
+    }
+}
+
+template <class T, int NR, bool SPLIT>
 __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_fwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
                                              const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
                                              int kcols, int c0) {
     extern __shared__ unsigned char smraw[];
     const FrontDesc d = D[fronts[blockIdx.x]];
     const int p = d.p, f = d.p + d.q, n = d.vlen;
-    T *v = reinterpret_cast<T *>(smraw);
-    T *xb = v + (int64_t)f * NR;   // the copy of x_B (32 x NR)
-    __shared__ T dblk[32][33];      // L[B,B]^{-1}, lower triangle
+    T *v = reinterpret_cast<T *>(smraw);   // the front's vector, f x NR
+    T *X = v + (int64_t)f * NR;             // x_B of every block, p x NR
     T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
-    for (int i = threadIdx.x; i < f; i += blockDim.x)
+    // rows updated block by block: the pivot rows only (SPLIT), or the structure rows too
+    const int rend = SPLIT ? p : f;
+    for (int i = threadIdx.x; i < rend; i += blockDim.x)
 #pragma unroll
         for (int r = 0; r < NR; ++r) v[i + r * f] = i < p ? xs[(int64_t)r * n + d.first + i] : T(0);
     __syncthreads();
     const T *Lp = L + d.l_off;
+    // 1. the triangle (and, unless SPLIT, the rectangle block by block)
     for (int jb = 0; jb < p; jb += 32) {
         const int kb = min(32, p - jb);
         if (threadIdx.x < 32 * NR) {
             const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
-            xb[threadIdx.x] = j < kb ? v[jb + j + r * f] : T(0);
-        }
-        // stage the inverse block with coalesced loads (column j contiguous)
-        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-            const int i = idx & 31, j = idx >> 5;
-            dblk[i][j] = (i < kb && j < kb && i >= j) ? Lp[(jb + i) + (int64_t)(jb + j) * f] : T(0);
+            if (j < kb) X[jb + j + r * p] = v[jb + j + r * f];
         }
         __syncthreads();
-        const T *col0 = Lp + (int64_t)jb * f;
-        if (threadIdx.x < kb) {
-            // rows of B (warp 0, from shared memory): y_B = L[B,B]^{-1} x_B
-            const int li = threadIdx.x;
+        for (int i = jb + threadIdx.x; i < rend; i += blockDim.x) {
             T acc[NR];
+            fwd_row<T, NR>(Lp + (int64_t)jb * f, f, i, kb, X + jb, p, acc);
+            if (i < jb + kb) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] = T(0);
-#pragma unroll 8
-            for (int j = 0; j < 32; ++j)
-#pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] += dblk[li][j] * xb[j + 32 * r];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) v[jb + li + r * f] = acc[r];
-        }
-        if (kb == 32 && NR > 1) {
-            // full block, several right-hand sides: the row's loads in four groups of
-            // eight, keeping the registers of NR accumulators affordable
-            for (int i = jb + 32 + threadIdx.x; i < f; i += blockDim.x) {
-                T acc[NR];
-#pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] = T(0);
-#pragma unroll
-                for (int jc = 0; jc < 32; jc += 8) {
-                    T l[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) l[j] = col0[i + (int64_t)(jc + j) * f];
-#pragma unroll
-                    for (int r = 0; r < NR; ++r)
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[r] += l[j] * xb[jc + j + 32 * r];
-                }
-#pragma unroll
-                for (int r = 0; r < NR; ++r) v[i + r * f] -= acc[r];
-            }
-        } else if (kb == 32) {
-            // full block: the row's 32 loads before any arithmetic
-            for (int i = jb + 32 + threadIdx.x; i < f; i += blockDim.x) {
-                T l[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) l[j] = col0[i + (int64_t)j * f];
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    T a0 = T(0), a1 = T(0);
-#pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        a0 += l[j] * xb[j + 32 * r];
-                        a1 += l[j + 1] * xb[j + 1 + 32 * r];
-                    }
-                    v[i + r * f] -= a0 + a1;
-                }
-            }
-        } else {
-            for (int i = jb + kb + threadIdx.x; i < f; i += blockDim.x) {
-                T acc[NR];
-#pragma unroll
-                for (int r = 0; r < NR; ++r) acc[r] = T(0);
-                for (int j = 0; j < kb; ++j) {
-                    const T l = col0[i + (int64_t)j * f];
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[r] += l * xb[j + 32 * r];
-                }
+                for (int r = 0; r < NR; ++r) v[i + r * f] = acc[r];
+            } else {
 #pragma unroll
                 for (int r = 0; r < NR; ++r) v[i + r * f] -= acc[r];
             }
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < f; i += blockDim.x) {
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            if (i < p) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
-            else atomicAdd(xs + (int64_t)r * n + rows[d.row_off + i], v[i + r * f]);
+        for (int r = 0; r < NR; ++r) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
+    if constexpr (!SPLIT) {
+        for (int i = p + threadIdx.x; i < f; i += blockDim.x)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) atomicAdd(xs + (int64_t)r * n + rows[d.row_off + i], v[i + r * f]);
+    } else {
+        // 2. the rectangle
+        for (int i = p + threadIdx.x; i < f; i += blockDim.x) {
+            T sum[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sum[r] = T(0);
+            for (int jb = 0; jb < p; jb += 32) {
+                T acc[NR];
+                fwd_row<T, NR>(Lp + (int64_t)jb * f, f, i, min(32, p - jb), X + jb, p, acc);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) sum[r] += acc[r];
+            }
+            const int gi = rows[d.row_off + i];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) atomicAdd(xs + (int64_t)r * n + gi, -sum[r]);
         }
     }
 }
 
-// Backward substitution for the fronts of one level, one CTA per front: for
-// each block B of 32 pivots from the last to the first,
-//   x_B = L[B,B]^{-T} y_B - W[i,B]^T x_i   (rows i below B),
-// i.e. one sum down each column of the block over the rows from B to the end
-// of the front (the rows of B with +, the rows below with -).  The rows of B
-// are negated in shared memory first, so every row enters the sum with the
-// same sign and x_B = -(sum).  Warp w takes the row tiles w, w + nw, ... of
-// 32 rows: lane l loads row r0 + l of the 32 columns (coalesced per column)
-// into registers, writes it transposed into the warp's 32 x 33 tile, and then
-// lane j accumulates column j over the tile's 32 rows from shared memory --
-// one FMA per nonzero and no per-column shuffle reduction; the next tile's
-// loads are in flight meanwhile.  The nw partial sums of each column are added
-// once per block.  No serial triangular solve remains.
+// Column sums of one warp over a 32-column block of a front panel (column c
+// at cb + c ld, c < kb): a[r] (lane j) = sum over rows i of W[i, j] v[i + r ld_v],
+// the rows taken in passes of SPAN = 32 G rows starting at rows rs, rs + step,
+// ... below rend.  Lane l loads row r0 + l of the columns (coalesced per
+// column) into registers, writes it transposed into the warp's 32 x 33 tile,
+// and lane j accumulates column j over the tile's rows from shared memory: one
+// FMA per entry, no shuffle reduction per column.  The columns are read 2^LW
+// wide: LW = 5 for a full block, the next pass's loads in flight meanwhile; a
+// short block (kb <= 16) is read 16, 8 or 4 wide, one pass then covering
+// G = 2^(5-LW) row tiles (tile g in register slots and lanes [g 2^LW,
+// (g+1) 2^LW)) whose partial sums of a column are added by shuffles at the
+// end -- the FMAs that a 32-wide pass would spend on the missing columns are
+// saved.  On return every lane j holds the sums of column j mod 2^LW.
+template <class T, int NR, int LW>
+__device__ __forceinline__ void warp_col_sums(const T *__restrict__ cb, int64_t ld, int kb, int rs, int rend, int step,
+                                              const T *v, int fv, T *tile, int lane, T a[NR]) {
+    constexpr int G = 32 >> LW, WM = (1 << LW) - 1;
+    constexpr bool PREFETCH = LW == 5;
+    T acc[NR], acc2[NR];   // two chains of FMAs per column
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = acc2[r] = T(0);
+    T w[32];
+    auto load = [&](int r0) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int i = r0 + 32 * (j >> LW) + lane;
+            w[j] = (i < rend && (j & WM) < kb) ? cb[i + (int64_t)(j & WM) * ld] : T(0);
+        }
+    };
+    int r0 = rs;
+    if (PREFETCH && r0 < rend) load(r0);
+    const int vg = 32 * (lane >> LW);   // this lane's tile within the pass
+    for (; r0 < rend; r0 += step) {
+        if (!PREFETCH) load(r0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[j * 33 + lane] = w[j];
+        __syncwarp();
+        if (PREFETCH && r0 + step < rend) load(r0 + step);
+        const int vb = r0 + vg;
+        const T *tl = tile + lane * 33;
+        if (r0 + 32 * G <= rend) {
+#pragma unroll
+            for (int ii = 0; ii < 32; ii += 2) {
+                const T t0 = tl[ii], t1 = tl[ii + 1];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    acc[r] += t0 * v[vb + ii + r * fv];
+                    acc2[r] += t1 * v[vb + ii + 1 + r * fv];
+                }
+            }
+        } else {
+            const int cnt = min(32, rend - vb);
+            for (int ii = 0; ii < cnt; ++ii) {
+                const T t = tl[ii];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] += t * v[vb + ii + r * fv];
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        T x = acc[r] + acc2[r];
+#pragma unroll
+        for (int o = 1 << LW; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        a[r] = x;
+    }
+}
+
+template <class T, int NR>
+__device__ __forceinline__ void warp_col_sums_short(const T *__restrict__ cb, int64_t ld, int kb, int rs, int rend,
+                                                    int passes, const T *v, int fv, T *tile, int lane, T a[NR]) {
+    // passes = stride between this warp's passes, counted in passes; a pass spans 32 (32 / 2^LW) rows
+    if (kb > 8) warp_col_sums<T, NR, 4>(cb, ld, kb, rs, rend, passes * 64, v, fv, tile, lane, a);
+    else if (kb > 4) warp_col_sums<T, NR, 3>(cb, ld, kb, rs, rend, passes * 128, v, fv, tile, lane, a);
+    else warp_col_sums<T, NR, 2>(cb, ld, kb, rs, rend, passes * 256, v, fv, tile, lane, a);
+}
+
+// Backward substitution for the fronts of one level, one CTA per front.  The
+// panel of a front is its pivot rows (the triangle, in partitioned-inverse
+// form) over its structure rows (a q x p rectangle).  With u_c = sum over
+// structure rows i of W[i, c] x_i, for each block B of 32 pivots from the last
+// to the first
+//   x_B = L[B,B]^{-T} y_B - W[i,B]^T x_i (later pivot rows i) - u_B.
+//   1. u for all columns at once: the rectangle's transposed product has no
+//      dependence between blocks, so the warps stream it without a block
+//      barrier, warp w taking column blocks w, w + nw, ... (or, when there are
+//      fewer blocks than warps, g = nw / blocks warps per block, each every
+//      g-th row tile, their partial sums added once).
+//   2. the triangle, block by block: the rows of B are negated first so every
+//      row enters one column sum with the same sign, the warps take row tiles
+//      of the pivot rows from B on, and x_B = -(sum + u_B).
+// One FMA per stored entry; no serial triangular solve remains.
 template <class T, int NR>
 __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict__ fronts, const FrontDesc *__restrict__ D,
                                              const T *__restrict__ L, const int *__restrict__ rows, T *__restrict__ x,
@@ -781,78 +900,101 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd(const int *__restrict
     const int p = d.p, f = d.p + d.q, n = d.vlen;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T *v = reinterpret_cast<T *>(smraw);      // the front's vector, f x NR
-    T *red = v + (int64_t)f * NR;               // NR x nw x 32 partial column sums
+    T *u = v + (int64_t)f * NR;                 // structure-row sums per pivot column, p x NR
+    T *red = u + (int64_t)p * NR;               // NR x nw x 32 partial column sums
     T *tile = red + 32 * NR * nw + warp * (32 * 33);   // this warp's transposed row tile
     T *xs = x + d.vec_off * kcols + (int64_t)c0 * n;
     for (int i = threadIdx.x; i < f; i += blockDim.x)
 #pragma unroll
         for (int r = 0; r < NR; ++r)
             v[i + r * f] = i < p ? xs[(int64_t)r * n + d.first + i] : xs[(int64_t)r * n + rows[d.row_off + i]];
-    __syncthreads();
     if (p == 0) return;
     const T *Lp = L + d.l_off;
+    const int nbf = p >> 5, kl = p & 31, nb = nbf + (kl ? 1 : 0);
+    // 1. structure rows
+    if (f > p) {
+        const int g = nb >= nw ? 1 : nw / nb, cstep = nw / g, c_first = warp / g, sub = warp % g;
+        __syncthreads();
+        T a[NR];
+        int cb = c_first;
+        for (; cb < nbf; cb += cstep) {
+            warp_col_sums<T, NR, 5>(Lp + (int64_t)32 * cb * f, f, 32, p + 32 * sub, f, 32 * g, v, f, tile, lane, a);
+            if (g == 1) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) u[32 * cb + lane + r * p] = a[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) red[(r * nw + warp) * 32 + lane] = a[r];
+            }
+        }
+        if (cb == nbf && kl > 0) {
+            // the short last block, read narrow when it has at most 16 columns
+            if (kl > 16) {
+                warp_col_sums<T, NR, 5>(Lp + (int64_t)32 * cb * f, f, kl, p + 32 * sub, f, 32 * g, v, f, tile, lane,
+                                        a);
+            } else {
+                const int span = 32 * (32 >> (kl > 8 ? 4 : (kl > 4 ? 3 : 2)));
+                warp_col_sums_short<T, NR>(Lp + (int64_t)32 * cb * f, f, kl, p + span * sub, f, g, v, f, tile, lane,
+                                           a);
+            }
+            if (g == 1) {
+                if (lane < kl)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) u[32 * cb + lane + r * p] = a[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) red[(r * nw + warp) * 32 + lane] = a[r];
+            }
+        }
+        __syncthreads();
+        if (g > 1)
+            for (int c = threadIdx.x; c < 32 * NR * nb; c += blockDim.x) {
+                const int r = c / (32 * nb), cc = c % (32 * nb), j = cc & 31, b = cc >> 5;
+                if (cc >= p) continue;
+                T s = T(0);
+                for (int k = 0; k < g; ++k) s += red[(r * nw + b * g + k) * 32 + j];
+                u[cc + r * p] = s;
+            }
+    } else {
+        for (int c = threadIdx.x; c < p * NR; c += blockDim.x) u[c] = T(0);
+    }
+    __syncthreads();
+    // 2. the triangle
     int jb = ((p - 1) / 32) * 32;
     if (threadIdx.x < 32 * NR) {
         const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
-        if (j < min(32, p - jb)) v[jb + j + r * f] = -v[jb + j + r * f];
+        if (j < p - jb) v[jb + j + r * f] = -v[jb + j + r * f];
     }
     __syncthreads();
-    for (; jb >= 0; jb -= 32) {
-        const int kb = min(32, p - jb);
-        const T *cb = Lp + (int64_t)jb * f;      // column jb + j starts at cb + j f
-        T acc[NR], acc2[NR];   // two chains of FMAs per column
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r] = acc2[r] = T(0);
-        T w[32];
-        int r0 = jb + 32 * warp;
-        if (r0 < f) {
-            const int i = r0 + lane;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) w[j] = (i < f && j < kb) ? cb[i + (int64_t)j * f] : T(0);
-        }
-        for (; r0 < f; r0 += 32 * nw) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) tile[j * 33 + lane] = w[j];
-            __syncwarp();
-            const int rn = r0 + 32 * nw;
-            if (rn < f) {
-                const int i = rn + lane;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) w[j] = (i < f && j < kb) ? cb[i + (int64_t)j * f] : T(0);
-            }
-            const int cnt = min(32, f - r0);
-            const T *tl = tile + lane * 33;
-            if (cnt == 32) {
-#pragma unroll
-                for (int ii = 0; ii < 32; ii += 2) {
-                    const T t0 = tl[ii], t1 = tl[ii + 1];
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        acc[r] += t0 * v[r0 + ii + r * f];
-                        acc2[r] += t1 * v[r0 + ii + 1 + r * f];
-                    }
-                }
-            } else {
-                for (int ii = 0; ii < cnt; ++ii) {
-                    const T t = tl[ii];
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) acc[r] += t * v[r0 + ii + r * f];
-                }
-            }
-            __syncwarp();
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) red[(r * nw + warp) * 32 + lane] = acc[r] + acc2[r];
+    // column sums of the block at jb (partial per warp in red) -> x_B; negate the next block's rows
+    auto finish = [&](int jb, int kb) {
         __syncthreads();
         if (threadIdx.x < 32 * NR) {
             const int j = threadIdx.x & 31, r = threadIdx.x >> 5;
             T s = T(0);
             for (int ww = 0; ww < nw; ++ww) s += red[(r * nw + ww) * 32 + j];
-            if (j < kb) v[jb + j + r * f] = -s;
+            if (j < kb) v[jb + j + r * f] = -(s + u[jb + j + r * p]);
             // the next block's rows (read from the next step on) enter its sum negated
             if (jb >= 32) v[jb - 32 + j + r * f] = -v[jb - 32 + j + r * f];
         }
         __syncthreads();
+    };
+    T a[NR];
+    if (kl > 0 && kl <= 16) {
+        // a short last block, read narrow (once per front, before the full blocks)
+        const int span = 32 * (32 >> (kl > 8 ? 4 : (kl > 4 ? 3 : 2)));
+        warp_col_sums_short<T, NR>(Lp + (int64_t)jb * f, f, kl, jb + span * warp, p, nw, v, f, tile, lane, a);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) red[(r * nw + warp) * 32 + lane] = a[r];
+        finish(jb, kl);
+        jb -= 32;
+    }
+    for (; jb >= 0; jb -= 32) {
+        const int kb = min(32, p - jb);
+        warp_col_sums<T, NR, 5>(Lp + (int64_t)jb * f, f, kb, jb + 32 * warp, p, 32 * nw, v, f, tile, lane, a);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) red[(r * nw + warp) * 32 + lane] = a[r];
+        finish(jb, kb);
     }
     for (int i = threadIdx.x; i < p; i += blockDim.x)
 #pragma unroll
@@ -933,7 +1075,6 @@ __global__ void __launch_bounds__(SWEEP_MAX_THREADS) k_bwd_shfl(const int *__res
         for (int r = 0; r < NR; ++r) xs[(int64_t)r * n + d.first + i] = v[i + r * f];
 }
 
-
 // Shared memory of the sweeps.  Forward: the front vector (f x NR) and the
 // copy of x_B (32 x NR), plus the static inverse block.  Backward: the front
 // vector, the partial column sums (NR x nw x 32) and one 32 x 33 tile per warp,
@@ -947,7 +1088,7 @@ template <class T, int NR>
 static size_t sweep_static_smem() {
     static const size_t v = [] {
         cudaFuncAttributes a{}, b{};
-        GL_CUDA(cudaFuncGetAttributes(&a, k_fwd<T, NR>));
+        GL_CUDA(cudaFuncGetAttributes(&a, k_fwd<T, NR, fwd_split<T>()>));
         GL_CUDA(cudaFuncGetAttributes(&b, k_bwd<T, NR>));
         return std::max<size_t>(1, std::max(a.sharedSizeBytes, b.sharedSizeBytes));
     }();
@@ -956,13 +1097,15 @@ static size_t sweep_static_smem() {
 
 template <class T, int NR>
 static size_t fwd_dyn_smem(int f) {
-    return ((size_t)std::max(f, 1) + 32) * NR * sizeof(T);
+    // front vector and the blocks' x_B (p <= f)
+    return (2 * (size_t)std::max(f, 1)) * NR * sizeof(T);
 }
 
 template <class T, int NR>
 static size_t bwd_dyn_smem(int f, int nthreads) {
+    // front vector and structure-row sums (p <= f), partial sums, one tile per warp
     const size_t nw = (size_t)nthreads / 32;
-    return ((size_t)std::max(f, 1) * NR + 32 * NR * nw + 33 * 32 * nw) * sizeof(T);
+    return ((size_t)std::max(f, 1) * NR * 2 + 32 * NR * nw + 33 * 32 * nw) * sizeof(T);
 }
 
 template <class T, int NR>
@@ -991,7 +1134,8 @@ static void ensure_sweep_smem(int max_f) {
     static SmemLimit limit;
     if (!sweep_fits<T, NR>(max_f)) return;
     raise_smem_limit(limit, SMEM_PER_CTA - sweep_static_smem<T, NR>(), [](size_t v) {
-        GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
+        GL_CUDA(cudaFuncSetAttribute(k_fwd<T, NR, fwd_split<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)v));
         GL_CUDA(cudaFuncSetAttribute(k_bwd<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
         GL_CUDA(cudaFuncSetAttribute(k_bwd_shfl<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
     });
@@ -1011,33 +1155,167 @@ void sweep_smem_for_plan(int max_f) {
     ensure_sweep_smem<float, 4>(max_f);
 }
 
+void level_clock_enable(FactorPlan &P, bool on) {
+    LevelClock &K = P.clock;
+    const size_t nlev = P.levels.size();
+    if (on && K.ev.size() != 2 * nlev + 1) {
+        for (cudaEvent_t e : K.ev)
+            if (e) cudaEventDestroy(e);
+        K.ev.assign(2 * nlev + 1, nullptr);
+        for (cudaEvent_t &e : K.ev) GL_CUDA(cudaEventCreate(&e));
+    }
+    K.fwd_ms.assign(nlev, 0.0);
+    K.bwd_ms.assign(nlev, 0.0);
+    K.calls = 0;
+    K.on = on;
+}
+
+// Events e[0..2 nlev]: e[nlev-1-d] before the forward launch of depth d,
+// e[nlev+d] before its backward launch, e[2 nlev] after the last launch.
+static void level_clock_fold(const FactorPlan &P) {
+    LevelClock &K = P.clock;
+    const int nlev = (int)P.levels.size();
+    GL_CUDA(cudaEventSynchronize(K.ev[2 * nlev]));
+    for (int d = 0; d < nlev; ++d) {
+        float a = 0, b = 0;
+        GL_CUDA(cudaEventElapsedTime(&a, K.ev[nlev - 1 - d], K.ev[nlev - d]));
+        GL_CUDA(cudaEventElapsedTime(&b, K.ev[nlev + d], K.ev[nlev + d + 1]));
+        K.fwd_ms[d] += a;
+        K.bwd_ms[d] += b;
+    }
+    K.calls += 1;
+}
+
+static int sweep_threads(const Level &Lv, bool bwd) {
+    if (Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW) return 512;
+    if (Lv.max_f <= GL_SWEEP_SMALL_F) return bwd ? GL_SWEEP_BWD_SMALL_THREADS : GL_SWEEP_FWD_SMALL_THREADS;
+    return bwd ? GL_SWEEP_BWD_THREADS : GL_SWEEP_FWD_THREADS;
+}
+
+// One level's forward or backward sweep over the fronts fr[0..nf) of that level.
+template <class T, int NR>
+static void launch_fwd(const FactorPlan &P, const Level &Lv, const int *fr, unsigned nf, const T *L, T *x, int kcols,
+                       int c0, cudaStream_t s) {
+    if (nf == 0) return;
+    const size_t sm = fwd_dyn_smem<T, NR>(Lv.max_f);
+    k_fwd<T, NR, fwd_split<T>()><<<nf, sweep_threads(Lv, false), sm, s>>>(fr, P.d_fr.p, L, P.d_rows.p, x, kcols,
+                                                                         c0);
+}
+
+template <class T, int NR>
+static void launch_bwd(const FactorPlan &P, const Level &Lv, const int *fr, unsigned nf, const T *L, T *x, int kcols,
+                       int c0, cudaStream_t s) {
+    if (nf == 0) return;
+    const int want = sweep_threads(Lv, true);
+    if (sizeof(T) == 4) {
+        const size_t sm = bwd_shfl_dyn_smem<T, NR>(Lv.max_f);
+        k_bwd_shfl<T, NR><<<nf, want, sm, s>>>(fr, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+    } else {
+        const int nt = bwd_threads<T, NR>(Lv.max_f, want);
+        const size_t sm = bwd_dyn_smem<T, NR>(Lv.max_f, nt);
+        k_bwd<T, NR><<<nf, nt, sm, s>>>(fr, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+    }
+}
+
+static HalfStreams &half_streams(const FactorPlan &P) {
+    if (!P.hs) {
+        auto h = std::make_unique<HalfStreams>();
+        int lo = 0, hi = 0;
+        GL_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        for (int k = 0; k < 2; ++k) {
+            GL_CUDA(cudaStreamCreateWithPriority(&h->hi[k], cudaStreamNonBlocking, hi));
+            GL_CUDA(cudaStreamCreateWithPriority(&h->lo[k], cudaStreamNonBlocking, lo));
+        }
+        GL_CUDA(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+        for (cudaEvent_t &e : h->ev) GL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        P.hs = std::move(h);
+    }
+    return *P.hs;
+}
+
+// Overlapped sweeps of the two halves of the subdomains (FactorPlan::overlap_top
+// = k > 0).  Half h: deep forward levels (depth >= k) on lo[h], then its top
+// levels (forward to the root and backward down to depth k - 1) on hi[h],
+// then its deep backward levels on lo[h].  The second half's deep forward
+// levels start when the first half enters its top levels.  The halves hold
+// disjoint subdomains, so they share no data.
+template <class T, int NR>
+static void solve_levels_overlap(const FactorPlan &P, const T *L, T *x, int kcols, int c0, cudaStream_t s) {
+    HalfStreams &H = half_streams(P);
+    const int nlev = (int)P.levels.size(), k = std::min(P.overlap_top, nlev);
+    GL_CUDA(cudaEventRecord(H.fork, s));
+    for (int h = 0; h < 2; ++h) {
+        GL_CUDA(cudaStreamWaitEvent(H.lo[h], H.fork, 0));
+        GL_CUDA(cudaStreamWaitEvent(H.hi[h], H.fork, 0));
+    }
+    auto part = [&](int h, int d, const int *&fr, unsigned &nf) {
+        const Level &Lv = P.levels[d];
+        const unsigned na = (unsigned)P.half_fronts[d];
+        fr = Lv.d_fronts.p + (h == 0 ? 0 : na);
+        nf = h == 0 ? na : (unsigned)Lv.fronts.size() - na;
+    };
+    // ev[3h]: half h reached its top levels; ev[3h+1]: its top levels are done; ev[3h+2]: all done
+    for (int h = 0; h < 2; ++h) {
+        if (h == 1) GL_CUDA(cudaStreamWaitEvent(H.lo[1], H.ev[0], 0));
+        for (int d = nlev - 1; d >= k; --d) {
+            const int *fr; unsigned nf;
+            part(h, d, fr, nf);
+            launch_fwd<T, NR>(P, P.levels[d], fr, nf, L, x, kcols, c0, H.lo[h]);
+        }
+        GL_CUDA(cudaEventRecord(H.ev[3 * h], H.lo[h]));
+        GL_CUDA(cudaStreamWaitEvent(H.hi[h], H.ev[3 * h], 0));
+        for (int d = k - 1; d >= 0; --d) {
+            const int *fr; unsigned nf;
+            part(h, d, fr, nf);
+            launch_fwd<T, NR>(P, P.levels[d], fr, nf, L, x, kcols, c0, H.hi[h]);
+        }
+        for (int d = 0; d < k; ++d) {
+            const int *fr; unsigned nf;
+            part(h, d, fr, nf);
+            launch_bwd<T, NR>(P, P.levels[d], fr, nf, L, x, kcols, c0, H.hi[h]);
+        }
+        GL_CUDA(cudaEventRecord(H.ev[3 * h + 1], H.hi[h]));
+    }
+    for (int h = 0; h < 2; ++h) {
+        GL_CUDA(cudaStreamWaitEvent(H.lo[h], H.ev[3 * h + 1], 0));
+        for (int d = k; d < nlev; ++d) {
+            const int *fr; unsigned nf;
+            part(h, d, fr, nf);
+            launch_bwd<T, NR>(P, P.levels[d], fr, nf, L, x, kcols, c0, H.lo[h]);
+        }
+        GL_CUDA(cudaEventRecord(H.ev[3 * h + 2], H.lo[h]));
+        GL_CUDA(cudaStreamWaitEvent(s, H.ev[3 * h + 2], 0));
+    }
+    GL_CUDA(cudaGetLastError());
+}
+
 template <class T, int NR>
 static void solve_levels(const FactorPlan &P, const T *L, T *x, int kcols, int c0, cudaStream_t s) {
     ensure_sweep_smem<T, NR>(P.max_f);
     const int nlev = (int)P.levels.size();
+    const bool timed = NR == 1 && kcols == 1 && P.clock.on && P.clock.ev.size() == 2 * (size_t)nlev + 1;
+    if (NR == 1 && kcols == 1 && P.overlap_top > 0 && !timed && P.n_sub >= 2) {
+        solve_levels_overlap<T, NR>(P, L, x, kcols, c0, s);
+        return;
+    }
+    auto mark = [&](int k) {
+        if (timed) GL_CUDA(cudaEventRecord(P.clock.ev[k], s));
+    };
     for (int dpt = nlev - 1; dpt >= 0; --dpt) {
+        mark(nlev - 1 - dpt);
         const Level &Lv = P.levels[dpt];
-        if (Lv.fronts.empty()) continue;
-        const size_t sm = fwd_dyn_smem<T, NR>(Lv.max_f);
-        const int nt = Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256;
-        k_fwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols, c0);
+        launch_fwd<T, NR>(P, Lv, Lv.d_fronts.p, (unsigned)Lv.fronts.size(), L, x, kcols, c0, s);
     }
     for (int dpt = 0; dpt < nlev; ++dpt) {
+        mark(nlev + dpt);
         const Level &Lv = P.levels[dpt];
-        if (Lv.fronts.empty()) continue;
-        const int want = Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW ? 512 : 256;
-        if (sizeof(T) == 4) {
-            const size_t sm = bwd_shfl_dyn_smem<T, NR>(Lv.max_f);
-            k_bwd_shfl<T, NR><<<(unsigned)Lv.fronts.size(), want, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x,
-                                                                          kcols, c0);
-        } else {
-            const int nt = bwd_threads<T, NR>(Lv.max_f, want);
-            const size_t sm = bwd_dyn_smem<T, NR>(Lv.max_f, nt);
-            k_bwd<T, NR><<<(unsigned)Lv.fronts.size(), nt, sm, s>>>(Lv.d_fronts.p, P.d_fr.p, L, P.d_rows.p, x, kcols,
-                                                                  c0);
-        }
+        launch_bwd<T, NR>(P, Lv, Lv.d_fronts.p, (unsigned)Lv.fronts.size(), L, x, kcols, c0, s);
     }
     GL_CUDA(cudaGetLastError());
+    if (timed) {
+        mark(2 * nlev);
+        level_clock_fold(P);
+    }
 }
 
 template <class T>

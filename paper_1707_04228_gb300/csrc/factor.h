@@ -53,6 +53,56 @@ struct Level {
     DBuf<int> d_fronts, d_child[2];
 };
 
+// Per-level timing of the sweeps (gl_profile_levels): while on, every
+// factor_solve with one right-hand side records a CUDA event before each
+// level's launch and after the last, waits for the last one and adds the
+// level times to fwd_ms / bwd_ms (indexed by depth).
+struct LevelClock {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<double> fwd_ms, bwd_ms;
+    int64_t calls = 0;
+    LevelClock() = default;
+    LevelClock(const LevelClock &) = delete;
+    LevelClock &operator=(const LevelClock &) = delete;
+    LevelClock(LevelClock &&o) noexcept { swap(o); }
+    LevelClock &operator=(LevelClock &&o) noexcept {
+        if (this != &o) swap(o);
+        return *this;
+    }
+    ~LevelClock() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    void swap(LevelClock &o) noexcept {
+        std::swap(on, o.on);
+        ev.swap(o.ev);
+        fwd_ms.swap(o.fwd_ms);
+        bwd_ms.swap(o.bwd_ms);
+        std::swap(calls, o.calls);
+    }
+};
+
+// Streams and events of the overlapped sweeps (FactorPlan::overlap_top): per
+// half of the subdomains a high-priority stream for its top levels and a
+// default-priority stream for its deep levels.
+struct HalfStreams {
+    cudaStream_t hi[2] = {}, lo[2] = {};
+    cudaEvent_t fork = nullptr, ev[6] = {};
+    HalfStreams() = default;
+    HalfStreams(const HalfStreams &) = delete;
+    HalfStreams &operator=(const HalfStreams &) = delete;
+    ~HalfStreams() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        for (int h = 0; h < 2; ++h) {
+            if (hi[h]) cudaStreamDestroy(hi[h]);
+            if (lo[h]) cudaStreamDestroy(lo[h]);
+        }
+    }
+};
+
 struct FactorPlan {
     int n_sub = 0;
     std::vector<int64_t> vec_off, vec_len;   // per subdomain
@@ -67,6 +117,15 @@ struct FactorPlan {
     bool tc_update = true;                   // FP32 factors: trailing updates on the tensor cores
     bool s20 = false;                        // serendipity elements: element matrices P^T K_Q2 P
     int last_groups = 0;                     // groups the last numeric_factor used
+    mutable LevelClock clock;                // per-level sweep timing (off unless profiling)
+    // > 0: single right-hand-side sweeps split the subdomains in two halves
+    // whose sweeps overlap -- the second half starts when the first reaches
+    // its top `overlap_top` levels, and those levels of either half run on a
+    // high-priority stream -- so that the deep levels of one half fill the
+    // SMs the few large fronts of the other half's top levels leave idle.
+    int overlap_top = 0;
+    std::vector<int> half_fronts;            // per level: fronts of the first half (a prefix of the list)
+    mutable std::unique_ptr<HalfStreams> hs;
     // device
     DBuf<FrontDesc> d_fr;
     DBuf<int> d_rows, d_rel, d_pair_elem;
@@ -102,6 +161,9 @@ void syrk_tc_level(const int *d_fronts, int n_fronts, const FrontDesc *d_fr, int
 // x[vec_off*kcols + c*n + i] (kcols = 1: plain concatenated local vectors).
 template <class T>
 void factor_solve(const FactorPlan &P, const T *L, T *x, int kcols, cudaStream_t s);
+
+// Switch the per-level sweep timing on (resetting it) or off.
+void level_clock_enable(FactorPlan &P, bool on);
 
 // local <-> global transfers: xl[i] = (T) r[gdof[i]]; z[gdof[i]] += xl[i]
 template <class T>

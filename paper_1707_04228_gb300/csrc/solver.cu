@@ -275,8 +275,12 @@ void prof_end(gl_ctx *c, int ph) {
 
 int64_t factor_solve_launches(const FactorPlan &P) {
     int64_t n = 0;
-    for (auto &L : P.levels)
-        if (!L.fronts.empty()) n += 2;
+    const bool halves = P.overlap_top > 0 && P.n_sub >= 2 && !P.clock.on;
+    for (size_t d = 0; d < P.levels.size(); ++d) {
+        const int64_t nf = (int64_t)P.levels[d].fronts.size(), na = P.half_fronts[d];
+        if (halves) n += 2 * ((na > 0 ? 1 : 0) + (nf - na > 0 ? 1 : 0));
+        else if (nf > 0) n += 2;
+    }
     return n;
 }
 
@@ -332,6 +336,13 @@ void apply_prec(gl_ctx *c, const double *r, double *z) {
         prof_end(c, PH_COARSE);
         g_launches += 3;
     }
+}
+
+// Top levels of the overlapped two-half sweeps (0: sequential sweeps).  The
+// default counts every level as top: the two halves sweep concurrently.
+int sweep_overlap_top(const gl_opts &o) {
+    if (o.sweep_overlap < 0) return 0;
+    return o.sweep_overlap > 0 ? o.sweep_overlap : 1 << 20;
 }
 
 void setup(gl_ctx *c, const gl_opts &o) {
@@ -418,6 +429,7 @@ void setup(gl_ctx *c, const gl_opts &o) {
     }
     c->PD.ws_budget_bytes = c->opts.factor_ws_bytes > 0 ? c->opts.factor_ws_bytes : 6e9;
     c->PD.tc_update = c->opts.fp32_update == 0;
+    c->PD.overlap_top = sweep_overlap_top(c->opts);
     c->PD.s20 = m.element == 1;
     stamp(c, "Dirichlet symbolic");
     if (std::getenv("GL_VERBOSE")) {
@@ -471,6 +483,7 @@ void setup(gl_ctx *c, const gl_opts &o) {
     c->S.alloc(1);
     if (!c->h_pin) GL_CUDA(cudaMallocHost(&c->h_pin, 8 * sizeof(double)));
     GL_CUDA(cudaStreamSynchronize(s));
+    if (c->prof.on) level_clock_enable(c->PD, true);
     c->ready = true;
     c->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -1501,6 +1514,7 @@ int gl_profile(gl_ctx *c, int enable) {
             for (auto &e : P.ev) cudaEventDestroy(e);
         }
         P.on = enable != 0;
+        if (c->ready) level_clock_enable(c->PD, P.on);
         for (int i = 0; i < PH_N; ++i) {
             P.ms[i] = 0;
             P.count[i] = 0;
@@ -1536,6 +1550,35 @@ int gl_profile_read(gl_ctx *c, gl_profile_data *out) {
         }
         out->factor_groups = c->PD.last_groups;
         out->eig_groups = c->co.n_groups;
+    });
+}
+
+int gl_profile_levels(gl_ctx *c, int max_levels, double *fwd_ms, double *bwd_ms, int64_t *fronts,
+                      int64_t *nonzeros, int64_t *padded, int *max_front, int *n_levels, int64_t *calls) {
+    return guard([&] {
+        require_ctx(c);
+        if (!c->ready) fail(GL_ERR_STATE, "gl_profile_levels before gl_setup");
+        GL_REQUIRE(max_levels >= 0, "max_levels must be >= 0");
+        const FactorPlan &P = c->PD;
+        const int nlev = (int)P.levels.size();
+        if (n_levels) *n_levels = nlev;
+        if (calls) *calls = P.clock.calls;
+        for (int d = 0; d < std::min(nlev, max_levels); ++d) {
+            const Level &Lv = P.levels[d];
+            int64_t nz = 0, pad = 0;
+            for (int g : Lv.fronts) {
+                const FrontDesc &fd = P.fr[g];
+                nz += (int64_t)fd.p * (fd.p + 1) / 2 + (int64_t)fd.p * fd.q;
+                for (int jb = 0; jb < fd.p; jb += 32) pad += 32 * (int64_t)(fd.p + fd.q - jb);
+            }
+            const bool have = d < (int)P.clock.fwd_ms.size();
+            if (fwd_ms) fwd_ms[d] = have ? P.clock.fwd_ms[d] : 0.0;
+            if (bwd_ms) bwd_ms[d] = have ? P.clock.bwd_ms[d] : 0.0;
+            if (fronts) fronts[d] = (int64_t)Lv.fronts.size();
+            if (nonzeros) nonzeros[d] = nz;
+            if (padded) padded[d] = pad;
+            if (max_front) max_front[d] = Lv.max_f;
+        }
     });
 }
 

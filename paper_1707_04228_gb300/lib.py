@@ -44,7 +44,8 @@ class gl_opts(C.Structure):
     _fields_ = [("px", C.c_int), ("py", C.c_int), ("pz", C.c_int), ("overlap", C.c_int), ("nev", C.c_int),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("resid_period", C.c_int),
                 ("tol", C.c_double), ("sigma", C.c_double), ("eig_iters", C.c_int),
-                ("factor_ws_bytes", C.c_double), ("eig_group_bytes", C.c_double), ("fp32_update", C.c_int)]
+                ("factor_ws_bytes", C.c_double), ("eig_group_bytes", C.c_double), ("fp32_update", C.c_int),
+                ("sweep_overlap", C.c_int)]
 
 
 class gl_info(C.Structure):
@@ -102,6 +103,8 @@ SIGNATURES = {
     "gl_batch_destroy": (None, [C.c_void_p]),
     "gl_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "gl_profile_read": (C.c_int, [C.c_void_p, C.POINTER(gl_profile_data)]),
+    "gl_profile_levels": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "gl_kernel_launches": (C.c_longlong, []),
     "gl_fp64_peak_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                      C.POINTER(C.c_double)]),
@@ -226,10 +229,11 @@ class Solver:
 
     def setup(self, px, py, pz, overlap=1, nev=8, tol=1e-10, max_iter=2000, precision=GL_PREC_FP64,
               resid_period=50, sigma=0.0, eig_iters=0, factor_ws_bytes=0.0, eig_group_bytes=0.0,
-              fp32_update=0):
+              fp32_update=0, sweep_overlap=0):
         o = gl_opts(px=px, py=py, pz=pz, overlap=overlap, nev=nev, max_iter=max_iter, precision=precision,
                     resid_period=resid_period, tol=tol, sigma=sigma, eig_iters=eig_iters,
-                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes, fp32_update=fp32_update)
+                    factor_ws_bytes=factor_ws_bytes, eig_group_bytes=eig_group_bytes, fp32_update=fp32_update,
+                    sweep_overlap=sweep_overlap)
         _check(self.lib, self.lib.gl_setup(self.ctx, C.byref(o)))
 
     @classmethod
@@ -351,6 +355,22 @@ class Solver:
         d = gl_profile_data()
         _check(self.lib, self.lib.gl_profile_read(self.ctx, C.byref(d)))
         return d.as_dict()
+
+    def profile_levels(self):
+        """gl_profile_levels: per dissection level, the timed forward/backward sweep milliseconds,
+        fronts, factor nonzeros, padded block entries and largest front, plus the number of timed
+        applications."""
+        n, calls = C.c_int(), C.c_int64()
+        _check(self.lib, self.lib.gl_profile_levels(self.ctx, 0, None, None, None, None, None, None, C.byref(n),
+                                                    C.byref(calls)))
+        L = n.value
+        fwd, bwd = np.zeros(L), np.zeros(L)
+        fronts, nz, pad = (np.zeros(L, dtype=np.int64) for _ in range(3))
+        maxf = np.zeros(L, dtype=np.int32)
+        _check(self.lib, self.lib.gl_profile_levels(self.ctx, L, _ptr(fwd), _ptr(bwd), _ptr(fronts), _ptr(nz),
+                                                    _ptr(pad), _ptr(maxf), C.byref(n), C.byref(calls)))
+        return {"calls": calls.value, "fwd_ms": fwd, "bwd_ms": bwd, "fronts": fronts, "nonzeros": nz,
+                "padded": pad, "max_front": maxf}
 
     def kernel_launches(self):
         return int(self.lib.gl_kernel_launches())
