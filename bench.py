@@ -45,6 +45,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PCG DOF-iterations/s at 1e-10 rel. residual; K*u HBM GB/s vs peak"
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one FP64
+# local-solve application per algorithmic byte, measured on the 32x8x23
+# corner (profiles/dram_local_sweeps_curved_corner_32x8x23.md); every panel is
+# read once, so it scales with the panels to the full-size workload.
+FP64_LOCAL_TRAFFIC_PER_ALG_BYTE = 1.076
 UNIT = "DOF-iterations/s"
 FP64_FMA_PER_SM_CLK = 2        # nominal FP64 FMA rate per SM and clock of this part (context only)
 
@@ -492,7 +497,9 @@ def main():
     fp64 = bpe == 8
     if fp64:
         roof = {"bound": "alu", "achieved": loc_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": loc_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": loc_tf / FP64_PEAK_TFLOPS, "traffic": FP64_LOCAL_TRAFFIC_PER_ALG_BYTE * loc_bytes,
+                "traffic_note": "bytes per application: the ratio of DRAM to algorithmic bytes measured by ncu "
+                                "on the 32x8x23 corner times this workload's algorithmic bytes",
                 "kernel": "local forward/backward supernodal sweeps (all levels) + gather/scatter",
                 "hbm_gbs": loc_bytes / (loc_ms / 1e3) / 1e9, "hbm_frac": loc_bytes / (loc_ms / 1e3) / 1e9 / hbm,
                 "peak_note": f"FP64 peak measured in this run by the FMA probe ({probe['n_sm']} SMs, nominal "

@@ -665,6 +665,14 @@ constexpr int SWEEP_WIDE_BELOW = 1216;  // fronts per level
 #ifndef GL_SWEEP_SMALL_F
 #define GL_SWEEP_SMALL_F 800
 #endif
+// Threads per CTA of the sweeps on levels with fewer than SWEEP_WIDE_BELOW fronts.
+#ifndef GL_SWEEP_FWD_WIDE_THREADS
+#define GL_SWEEP_FWD_WIDE_THREADS 512
+#endif
+#ifndef GL_SWEEP_BWD_WIDE_THREADS
+#define GL_SWEEP_BWD_WIDE_THREADS 512
+#endif
+
 // The forward sweep of FP64 (FP32) factors treats the structure rows after the
 // triangle when GL_FWD_SPLIT64 (GL_FWD_SPLIT32) is 1, block by block otherwise.
 #ifndef GL_FWD_SPLIT64
@@ -1187,7 +1195,7 @@ static void level_clock_fold(const FactorPlan &P) {
 }
 
 static int sweep_threads(const Level &Lv, bool bwd) {
-    if (Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW) return 512;
+    if (Lv.fronts.size() < (size_t)SWEEP_WIDE_BELOW) return bwd ? GL_SWEEP_BWD_WIDE_THREADS : GL_SWEEP_FWD_WIDE_THREADS;
     if (Lv.max_f <= GL_SWEEP_SMALL_F) return bwd ? GL_SWEEP_BWD_SMALL_THREADS : GL_SWEEP_FWD_SMALL_THREADS;
     return bwd ? GL_SWEEP_BWD_THREADS : GL_SWEEP_FWD_THREADS;
 }
