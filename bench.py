@@ -46,9 +46,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PCG DOF-iterations/s at 1e-10 rel. residual; K*u HBM GB/s vs peak"
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one FP64
-# local-solve application per algorithmic byte, measured on the 32x8x23
-# corner (profiles/dram_local_sweeps_curved_corner_32x8x23.md); every panel is
-# read once, so it scales with the panels to the full-size workload.
+# local-solve application per algorithmic byte, measured over the 20 launches
+# of one application on the 151,011-DOF 32x8x23 corner; every panel is read
+# once, so it scales with the panels to the full-size workload.
 FP64_LOCAL_TRAFFIC_PER_ALG_BYTE = 1.076
 UNIT = "DOF-iterations/s"
 FP64_FMA_PER_SM_CLK = 2        # nominal FP64 FMA rate per SM and clock of this part (context only)
