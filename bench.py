@@ -477,9 +477,12 @@ def main():
            "d2h_bytes_per_step": 8 * N}
 
     # phase timing pass (separate from the timed steps)
-    s.profile(True)
+    s.profile(1)                 # phases in the solve's own schedule
     s.solve(f, out=u)
     prof = s.profile_read()
+    s.profile(2)                 # and every dissection level, the levels one after another
+    s.solve(f, out=u)
+    prof_seq = s.profile_read()
     lv = s.profile_levels()
     s.profile(False)
     hbm, hbm_src = peaks()
@@ -492,7 +495,8 @@ def main():
     ku_bytes = 16 * N + NE * (36 + 270) * 8                         # x in, y out, C_e and Gauss-point J^-1, w|J|
     ku_flops = NE * (2 * 5346 + 162)                                # collocation sum factorisation: FMA, MUL
     ku_ms = prof["ms_ku"] / max(prof["n_ku"], 1)
-    per_iter = {"ku_ms": ku_ms, "local_ms": loc_ms, "coarse_ms": prof["ms_coarse"] / max(prof["n_coarse"], 1)}
+    per_iter = {"ku_ms": ku_ms, "local_ms": loc_ms, "coarse_ms": prof["ms_coarse"] / max(prof["n_coarse"], 1),
+                "local_ms_levels_in_sequence": prof_seq["ms_local"] / max(prof_seq["n_local"], 1)}
     loc_tf = loc_flops / (loc_ms / 1e3) / 1e12
     fp64 = bpe == 8
     if fp64:

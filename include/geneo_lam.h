@@ -355,9 +355,13 @@ void gl_batch_destroy(gl_batch *batch);
 
 /* Measurement.  gl_profile(ctx, 1) switches on CUDA-event timing of the
  * solve's phases on the context's stream (matrix-free K u; local Schwarz
- * solves = gather + forward/backward sweeps over all factor levels + scatter;
- * coarse restrict/solve/prolong) and resets the accumulators; 0 switches it
- * off.  Timing adds a host wait before each phase is reused.
+ * solves = gather + forward/backward sweeps over all factor levels + scatter,
+ * in their normal schedule; coarse restrict/solve/prolong, which then runs
+ * after the local solves instead of beside them) and resets the
+ * accumulators; gl_profile(ctx, 2) also times every dissection level
+ * (gl_profile_levels), the levels then running one after another; 0
+ * switches timing off; other values are GL_ERR_INVALID_ARG.  Timing adds a
+ * host wait before each phase is reused.
  * gl_profile_read returns the accumulators and the sizes that turn them into
  * bandwidth and flop rates.  gl_kernel_launches returns the number of kernels
  * this library has launched from gl_solve and the gl_apply_* calls since it
@@ -381,7 +385,7 @@ typedef struct {
 int gl_profile(gl_ctx *ctx, int enable);
 int gl_profile_read(gl_ctx *ctx, gl_profile_data *out);
 /* Per dissection level of the local solves (Section 2.3), from the
- * preconditioner applications timed since gl_profile(ctx, 1) (CUDA events
+ * preconditioner applications timed since gl_profile(ctx, 2) (CUDA events
  * before every level's launch; each timed application waits for its last
  * launch).  For every depth d < min(max_levels, *n_levels): fwd_ms[d] and
  * bwd_ms[d], the summed milliseconds of that level's forward and backward

@@ -71,6 +71,7 @@ std::atomic<long long> g_launches(0);   // kernels launched by gl_solve / gl_app
 enum { PH_KU = 0, PH_LOCAL = 1, PH_COARSE = 2, PH_N = 3 };
 struct Prof {
     bool on = false;
+    bool levels = false;   // per-level sweep timing too (levels then run in sequence)
     cudaEvent_t ev[2 * PH_N] = {};
     double ms[PH_N] = {0, 0, 0};
     long long count[PH_N] = {0, 0, 0};
@@ -483,7 +484,7 @@ void setup(gl_ctx *c, const gl_opts &o) {
     c->S.alloc(1);
     if (!c->h_pin) GL_CUDA(cudaMallocHost(&c->h_pin, 8 * sizeof(double)));
     GL_CUDA(cudaStreamSynchronize(s));
-    if (c->prof.on) level_clock_enable(c->PD, true);
+    if (c->prof.levels) level_clock_enable(c->PD, true);
     c->ready = true;
     c->ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -1513,8 +1514,10 @@ int gl_profile(gl_ctx *c, int enable) {
             GL_CUDA(cudaStreamSynchronize(c->stream));
             for (auto &e : P.ev) cudaEventDestroy(e);
         }
+        GL_REQUIRE(enable >= 0 && enable <= 2, "gl_profile: enable must be 0, 1 or 2");
         P.on = enable != 0;
-        if (c->ready) level_clock_enable(c->PD, P.on);
+        P.levels = enable == 2;
+        if (c->ready) level_clock_enable(c->PD, P.levels);
         for (int i = 0; i < PH_N; ++i) {
             P.ms[i] = 0;
             P.count[i] = 0;

@@ -349,7 +349,10 @@ class Solver:
         return grad, self.last_adjoint_info
 
     def profile(self, enable=True):
-        _check(self.lib, self.lib.gl_profile(self.ctx, 1 if enable else 0))
+        """gl_profile: True or 1 times the solve's phases, 2 also every dissection level of the
+        local solves (levels then in sequence), False or 0 switches timing off."""
+        mode = 1 if enable is True else (0 if enable is False else int(enable))
+        _check(self.lib, self.lib.gl_profile(self.ctx, mode))
 
     def profile_read(self):
         d = gl_profile_data()

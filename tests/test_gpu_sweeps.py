@@ -94,10 +94,11 @@ def test_overlapped_halves(lib_mod, oracle_case):
 
 def test_level_profile(lib_mod, oracle_case):
     """gl_profile_levels: per-level sizes add up to the plan's totals, and the
-    timed sweeps cover every level that has fronts."""
+    timed sweeps cover every level that has fronts; with phase timing only
+    (gl_profile 1) no level is timed."""
     lam, mesh, sysm = oracle_case
     s = lib_mod.Solver.from_laminate(lam)
-    s.profile(True)
+    s.profile(2)
     s.solve()
     prof = s.profile_read()
     lv = s.profile_levels()
@@ -108,3 +109,8 @@ def test_level_profile(lib_mod, oracle_case):
     has = lv["fronts"] > 0
     assert np.all(lv["fwd_ms"][has] > 0) and np.all(lv["bwd_ms"][has] > 0)
     assert np.all(lv["max_front"][has] > 0)
+    s.profile(1)
+    s.solve()
+    assert s.profile_levels()["calls"] == 0
+    assert s.profile_read()["n_local"] >= 1
+    s.profile(False)
